@@ -1,0 +1,128 @@
+/*
+ * ldlt_rpm.h -- C ABI of the GB300 (sm_103a) symmetric indefinite factorisation
+ * over Z/pZ that reveals the rank profile matrix.
+ *
+ * Method: Dumas & Pernet, "Symmetric indefinite triangular factorization
+ * revealing the rank profile matrix" (arXiv 1802.10453).  The factorisation is
+ * P^T A P = L D L^T (abstract; A = P L D L^T P^T in Algorithms 2-4) with P a
+ * permutation, L unit lower triangular and D block diagonal with 1x1 blocks
+ * and 2x2 blocks [[0,x],[x,0]] (odd p) or [[0,x],[x,y]] (p = 2, the relaxed
+ * lower antitriangular blocks of Section 2.2).  Pivots follow the
+ * lexicographic search of Algorithm 4 (Section 5): for the next row, the
+ * diagonal of its Schur complement row if non-zero, else the first non-zero
+ * to its right, else the row is not a pivot.  The rank profile matrix is the
+ * pivoting matrix P Psi P^T (Section 2.1, Definitions 1 and 2), Psi being the
+ * support of D.
+ *
+ * All matrix and vector pointers are DEVICE pointers owned by the caller.
+ * Work is enqueued on `stream` (a cudaStream_t passed as void*; NULL = the
+ * legacy default stream).  Functions return 0 (LDLT_OK) or a negative
+ * LDLT_ERR_* code for errors the host can detect; no C++ exception crosses
+ * this boundary.  Errors found on the device (a bounded wait that ran out) are
+ * written to the caller's device status word.  Outputs are undefined when
+ * either is non-zero.
+ */
+#ifndef LDLT_RPM_H
+#define LDLT_RPM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define LDLT_OK              0
+#define LDLT_ERR_ARG        -1  /* n < 0, lda < n, a NULL pointer, unknown path   */
+#define LDLT_ERR_NOT_PRIME  -2  /* p < 2 or p composite                           */
+#define LDLT_ERR_P_RANGE    -3  /* p >= 2^31, or the FP64 path with p too large    */
+#define LDLT_ERR_WORKSPACE  -4  /* ws NULL or smaller than the queried size        */
+#define LDLT_ERR_CUDA       -5  /* a CUDA runtime call failed (launch, copy, ...)  */
+#define LDLT_ERR_TIMEOUT    -6  /* device only: a bounded spin-wait gave up        */
+#define LDLT_ERR_NO_DEVICE  -7  /* no sm_103 device visible                         */
+
+/* ---- arithmetic paths for the level-3 updates (SYRDK, Algorithm 2) ------ */
+/* FP64 form: residues carried in doubles, products accumulated with one
+ * reduction per block of k terms, k*((p-1)/2)^2 + 1.5p < 2^53 (p < 2^26.5). */
+#define LDLT_PATH_FP64      0
+/* Tensor form: residues split into signed 8-bit limbs held exactly in bf16,
+ * tcgen05.mma kind::f16 with FP32 accumulation (exact below 2^24), limbs
+ * recombined and reduced mod p once per output.  Any prime p < 2^31. */
+#define LDLT_PATH_TC        1
+
+/*
+ * ldlt_rpm_workspace_bytes -- size of the device workspace ldlt_rpm_factor
+ * needs for order n, prime p and the given path.  Pure host computation.
+ * Returns LDLT_OK and *bytes, or LDLT_ERR_ARG / LDLT_ERR_NOT_PRIME /
+ * LDLT_ERR_P_RANGE.
+ */
+int ldlt_rpm_workspace_bytes(int64_t n, uint32_t p, int path, size_t *bytes);
+
+/*
+ * ldlt_rpm_factor -- factor P^T A P = L D L^T mod p in place (the problem of
+ * the abstract; pivot order of Algorithm 4, Section 5; level-3 updates of
+ * Algorithm 2, Section 4).
+ *
+ *   n        order of A (n >= 0).
+ *   p        prime modulus, 2 <= p < 2^31.
+ *   A        n x n row-major uint32 with leading dimension lda (elements).
+ *            Input: the lower triangle with the diagonal is read; entries are
+ *            reduced mod p.  The upper triangle is ignored.
+ *            Output: strictly below the diagonal, L (row k of L is row k of
+ *            P^T A P; unit diagonal implicit; columns k >= rank are identity
+ *            columns); on the diagonal, D_kk.  The upper triangle is left
+ *            unspecified.
+ *   perm     int32[n]: perm[k] = original index of row/column k of P^T A P
+ *            (P e_k = e_perm[k]).  Pivots come in the order found, a before b
+ *            for a 2x2 pivot on rows a < b, then the non-pivot rows in
+ *            ascending order.
+ *   e        uint32[n]: e[k] = x when rows (k, k+1) form a 2x2 block, else 0.
+ *   rank     int64[1]: the rank r.
+ *   status   int32[1]: 0, or LDLT_ERR_TIMEOUT if a device wait gave up.
+ *   path     LDLT_PATH_FP64 or LDLT_PATH_TC.
+ *   ws       device workspace of at least ldlt_rpm_workspace_bytes() bytes,
+ *            256-byte aligned; owned by the caller, not retained after return.
+ *   stream   cudaStream_t as void*.
+ *
+ * The call enqueues work on `stream` and returns after the last kernel has
+ * been enqueued.  It reads back a few words per panel on that stream to size
+ * the next launches, so it synchronises `stream` internally; results are
+ * ready when the stream is.
+ */
+int ldlt_rpm_factor(int64_t n, uint32_t p, uint32_t *A, int64_t lda,
+                    int32_t *perm, uint32_t *e, int64_t *rank, int32_t *status,
+                    int path, void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * rpm_from_factor -- the rank profile matrix R_A = P Psi P^T (Section 2.1,
+ * Definition 1; Psi = support of D, for p = 2 the relaxed block's support is
+ * still the antidiagonal J, Section 2.2).
+ *
+ *   n, perm, e, rank   as returned by ldlt_rpm_factor (device pointers;
+ *                      rank is read on the device).
+ *   rpm_col            int32[n] output: rpm_col[i] = j if (R_A)_{ij} = 1,
+ *                      else -1.  R_A is a symmetric rook placement (Lemma 1).
+ * Returns LDLT_OK, LDLT_ERR_ARG or LDLT_ERR_CUDA.
+ */
+int rpm_from_factor(int64_t n, const int32_t *perm, const uint32_t *e,
+                    const int64_t *rank, int32_t *rpm_col, void *stream);
+
+/*
+ * ldlt_rpm_version -- library version as major*10000 + minor*100 + patch.
+ */
+int ldlt_rpm_version(void);
+
+/*
+ * ldlt_rpm_set_wait_budget_ns -- upper bound, in nanoseconds, on every
+ * spin-wait inside the factorisation kernels (default 2e9).  When a wait runs
+ * out the kernel writes LDLT_ERR_TIMEOUT to *status and returns.  Used by the
+ * failure-detection tests; 0 restores the default.
+ */
+void ldlt_rpm_set_wait_budget_ns(int64_t ns);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LDLT_RPM_H */

@@ -1,0 +1,31 @@
+"""GB300 (sm_103a) rank-profile-revealing symmetric factorisation mod p.
+
+Thin Python binding of the C ABI in ``include/ldlt_rpm.h`` (argument
+marshalling only; every step runs in the CUDA library).  PyTorch supplies
+device memory and streams.
+
+    import torch, paper_1802_10453_gb300 as lr
+    res = lr.factor(A_cuda_uint32_view, p, path=lr.PATH_TC)
+    rpm = lr.rpm_from_factor(res)
+"""
+from .binding import (  # noqa: F401
+    PATH_FP64,
+    PATH_TC,
+    LDLT_OK,
+    LDLT_ERR_ARG,
+    LDLT_ERR_NOT_PRIME,
+    LDLT_ERR_P_RANGE,
+    LDLT_ERR_WORKSPACE,
+    LDLT_ERR_CUDA,
+    LDLT_ERR_TIMEOUT,
+    LDLT_ERR_NO_DEVICE,
+    LdltError,
+    lib,
+    lib_path,
+    workspace_bytes,
+    factor,
+    factor_raw,
+    rpm_from_factor,
+    set_wait_budget_ns,
+    effective_ops,
+)

@@ -1,0 +1,159 @@
+"""ctypes binding of libldlt_rpm.so (C ABI of include/ldlt_rpm.h).
+
+Marshalling only: tensors are passed as raw device pointers; every computation
+runs in the CUDA library.  The library is loaded on first use and a missing
+library is an error -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(HERE, "libldlt_rpm.so")
+
+PATH_FP64 = 0
+PATH_TC = 1
+LDLT_OK = 0
+LDLT_ERR_ARG = -1
+LDLT_ERR_NOT_PRIME = -2
+LDLT_ERR_P_RANGE = -3
+LDLT_ERR_WORKSPACE = -4
+LDLT_ERR_CUDA = -5
+LDLT_ERR_TIMEOUT = -6
+LDLT_ERR_NO_DEVICE = -7
+_NAMES = {0: "LDLT_OK", -1: "LDLT_ERR_ARG", -2: "LDLT_ERR_NOT_PRIME", -3: "LDLT_ERR_P_RANGE",
+          -4: "LDLT_ERR_WORKSPACE", -5: "LDLT_ERR_CUDA", -6: "LDLT_ERR_TIMEOUT",
+          -7: "LDLT_ERR_NO_DEVICE"}
+
+EXPORTS = ["ldlt_rpm_workspace_bytes", "ldlt_rpm_factor", "rpm_from_factor", "ldlt_rpm_version",
+           "ldlt_rpm_set_wait_budget_ns"]
+
+
+class LdltError(RuntimeError):
+    def __init__(self, code, what=""):
+        super().__init__("%s (%d)%s" % (_NAMES.get(code, "?"), code, (": " + what) if what else ""))
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def lib():
+    """Load libldlt_rpm.so (raises if it was not built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_LIB_PATH):
+                raise RuntimeError("libldlt_rpm.so is missing: run __graft_entry__.build() "
+                                   "(python -m paper_1802_10453_gb300.build)")
+            L = ctypes.CDLL(_LIB_PATH)
+            c_i64, c_u32, c_vp, c_sz = ctypes.c_int64, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_size_t
+            L.ldlt_rpm_workspace_bytes.restype = ctypes.c_int
+            L.ldlt_rpm_workspace_bytes.argtypes = [c_i64, c_u32, ctypes.c_int, ctypes.POINTER(c_sz)]
+            L.ldlt_rpm_factor.restype = ctypes.c_int
+            L.ldlt_rpm_factor.argtypes = [c_i64, c_u32, c_vp, c_i64, c_vp, c_vp, c_vp, c_vp,
+                                          ctypes.c_int, c_vp, c_sz, c_vp]
+            L.rpm_from_factor.restype = ctypes.c_int
+            L.rpm_from_factor.argtypes = [c_i64, c_vp, c_vp, c_vp, c_vp, c_vp]
+            L.ldlt_rpm_version.restype = ctypes.c_int
+            L.ldlt_rpm_version.argtypes = []
+            L.ldlt_rpm_set_wait_budget_ns.restype = None
+            L.ldlt_rpm_set_wait_budget_ns.argtypes = [c_i64]
+            _lib = L
+    return _lib
+
+
+def workspace_bytes(n: int, p: int, path: int = PATH_TC) -> int:
+    out = ctypes.c_size_t(0)
+    rc = lib().ldlt_rpm_workspace_bytes(int(n), int(p), int(path), ctypes.byref(out))
+    if rc != LDLT_OK:
+        raise LdltError(rc, "workspace query")
+    return int(out.value)
+
+
+def set_wait_budget_ns(ns: int) -> None:
+    lib().ldlt_rpm_set_wait_budget_ns(int(ns))
+
+
+def effective_ops(n: int, r: int) -> float:
+    """Operation count of Section 6: r^3/3 + n^2 r - r^2 n."""
+    n, r = float(n), float(r)
+    return r ** 3 / 3.0 + n * n * r - r * r * n
+
+
+def factor_raw(n, p, A_ptr, lda, perm_ptr, e_ptr, rank_ptr, status_ptr, path, ws_ptr, ws_bytes,
+               stream_ptr) -> int:
+    return lib().ldlt_rpm_factor(int(n), int(p), A_ptr, int(lda), perm_ptr, e_ptr, rank_ptr,
+                                 status_ptr, int(path), ws_ptr, int(ws_bytes), stream_ptr)
+
+
+_ws_cache = {}
+
+
+def _workspace(nbytes: int, device):
+    import torch
+    key = (str(device),)
+    buf = _ws_cache.get(key)
+    if buf is None or buf.numel() < nbytes:
+        buf = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
+        _ws_cache[key] = buf
+    return buf
+
+
+def factor(A, p: int, path: int = PATH_TC, stream=None, workspace=None, check: bool = True) -> dict:
+    """Factor P^T A P = L D L^T mod p in place on the GPU.
+
+    A: CUDA tensor of shape (n, n) and dtype int32 (residues as 32-bit words),
+    rows contiguous; its lower triangle is read.  On return A holds L strictly
+    below the diagonal (rows in perm order) and D on the diagonal.
+    Returns dict(perm, e, rank, status) of CUDA tensors (rank, status: 1 element).
+    """
+    import torch
+    if not A.is_cuda or A.dtype not in (torch.int32,) or A.dim() != 2 or A.shape[0] != A.shape[1]:
+        raise LdltError(LDLT_ERR_ARG, "A must be a square int32 CUDA tensor")
+    if A.shape[0] > 0 and A.stride(1) != 1:
+        raise LdltError(LDLT_ERR_ARG, "rows of A must be contiguous")
+    n = A.shape[0]
+    dev = A.device
+    perm = torch.empty(n, dtype=torch.int32, device=dev)
+    e = torch.empty(n, dtype=torch.int32, device=dev)
+    rank = torch.zeros(1, dtype=torch.int64, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    nbytes = workspace_bytes(n, p, path)
+    ws = workspace if workspace is not None else _workspace(nbytes, dev)
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    lda = A.stride(0) if n > 0 else 1
+    rc = factor_raw(n, p, A.data_ptr(), lda, perm.data_ptr(), e.data_ptr(), rank.data_ptr(),
+                    status.data_ptr(), path, ws.data_ptr(), ws.numel(), stream.cuda_stream)
+    if rc != LDLT_OK:
+        raise LdltError(rc, "ldlt_rpm_factor")
+    res = dict(perm=perm, e=e, rank=rank, status=status, n=n, p=p)
+    if check:
+        stream.synchronize()
+        st = int(status.item())
+        if st != 0:
+            raise LdltError(st, "device status")
+    return res
+
+
+def rpm_from_factor(res: dict, stream=None):
+    """rpm_col[i] = j where (P Psi P^T)_ij = 1, else -1 (CUDA int32 tensor)."""
+    import torch
+    n = res["n"]
+    dev = res["perm"].device
+    out = torch.empty(n, dtype=torch.int32, device=dev)
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    rc = lib().rpm_from_factor(n, res["perm"].data_ptr(), res["e"].data_ptr(), res["rank"].data_ptr(),
+                               out.data_ptr(), stream.cuda_stream)
+    if rc != LDLT_OK:
+        raise LdltError(rc, "rpm_from_factor")
+    return out

@@ -1,0 +1,81 @@
+// field.cuh -- arithmetic in F = Z/pZ (p prime, p < 2^31) for the device.
+//
+// Residues are canonical uint32 in [0, p).  Reduction of a 64-bit value uses
+// Barrett's method (P. Barrett, "Implementing the Rivest Shamir and Adleman
+// public key encryption algorithm on a standard digital signal processor",
+// CRYPTO 1986) with mu = floor((2^64 - 1) / p): q = hi64(x * mu) underestimates
+// floor(x / p) by at most 2, so at most two corrections follow.
+//
+// Dot products accumulate exact 64-bit products without reducing each one:
+// products are < 2^62, and whenever the running sum reaches 2^63 a fixed
+// multiple M of p with 2^62 < M <= 2^63 is subtracted, so the sum never wraps.
+#pragma once
+#include <cstdint>
+
+struct FieldP {
+    uint32_t p;
+    uint32_t inv2;   // (p + 1) / 2, the inverse of 2 for odd p; 0 for p = 2
+    uint64_t mu;     // floor((2^64 - 1) / p)
+    uint64_t m63;    // multiple of p in (2^62, 2^63]
+};
+
+inline FieldP make_field(uint32_t p)
+{
+    FieldP f;
+    f.p = p;
+    f.inv2 = (p == 2) ? 0u : (p + 1u) / 2u;
+    f.mu = ~0ull / (uint64_t)p;
+    uint64_t pp = (uint64_t)p * (uint64_t)p;
+    f.m63 = ((1ull << 63) / pp) * pp;  // > 2^62 because pp < 2^62
+    return f;
+}
+
+__device__ __forceinline__ uint32_t fp_reduce64(uint64_t x, const FieldP &f)
+{
+    uint64_t q = __umul64hi(x, f.mu);
+    uint64_t r = x - q * (uint64_t)f.p;
+    if (r >= f.p) r -= f.p;
+    if (r >= f.p) r -= f.p;
+    return (uint32_t)r;
+}
+
+__device__ __forceinline__ uint32_t fp_mul(uint32_t a, uint32_t b, const FieldP &f)
+{
+    return fp_reduce64((uint64_t)a * (uint64_t)b, f);
+}
+
+__device__ __forceinline__ uint32_t fp_add(uint32_t a, uint32_t b, const FieldP &f)
+{
+    uint32_t s = a + b;  // < 2^32 since a, b < 2^31
+    return s >= f.p ? s - f.p : s;
+}
+
+__device__ __forceinline__ uint32_t fp_sub(uint32_t a, uint32_t b, const FieldP &f)
+{
+    return a >= b ? a - b : a + (f.p - b);
+}
+
+// acc += a * b without overflow (see the header comment).
+__device__ __forceinline__ void fp_mac(uint64_t &acc, uint32_t a, uint32_t b, const FieldP &f)
+{
+    acc += (uint64_t)a * (uint64_t)b;
+    acc -= (acc >> 63) * f.m63;
+}
+
+// Inverse of a != 0 modulo the prime p: extended Euclidean algorithm on
+// 32-bit values (the Bezout coefficient is tracked modulo p).
+__device__ __forceinline__ uint32_t fp_inv(uint32_t a, const FieldP &f)
+{
+    uint32_t r0 = f.p, r1 = a;
+    int64_t s0 = 0, s1 = 1;
+    while (r1 != 0) {
+        uint32_t q = r0 / r1;
+        uint32_t r2 = r0 - q * r1;
+        int64_t s2 = s0 - (int64_t)q * s1;
+        r0 = r1; r1 = r2;
+        s0 = s1; s1 = s2;
+    }
+    int64_t v = s0 % (int64_t)f.p;
+    if (v < 0) v += f.p;
+    return (uint32_t)v;
+}

@@ -1,0 +1,116 @@
+// ldlt_internal.cuh -- shared declarations of the CUDA library (not part of the ABI).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "field.cuh"
+
+// Panel geometry.  A panel takes at most KP_MAX pivots (L columns) from the
+// window of the first W0 remaining rows; its far rows are shared by helper CTAs.
+constexpr int KP_MAX = 128;
+constexpr int W0 = 256;
+constexpr int PANEL_THREADS = 256;   // one thread per window row
+constexpr int MAX_EVENTS = 2 * W0 + 4;
+
+// Row storage of the Schur complement and of L: leading dimension rounded up so
+// every row starts on a 256-byte boundary.
+inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+enum EventKind : int { EV_PIVOT1 = 1, EV_PIVOT2 = 2, EV_SCAN = 3, EV_END = 4 };
+
+// One message from the leader CTA to the helper CTAs (see panel.cu).
+struct Event {
+    int kind;
+    int a, b;        // compact rows of the pivot (b only for 2x2)
+    int np;          // pivots before this event (length of the v vectors)
+    uint32_t s0;     // 1x1: d^{-1}; 2x2: x^{-1}
+    uint32_t s1;     // 2x2: delta (y/2 for odd p, y for p = 2)
+    int scan_id;     // EV_SCAN: sequence number of the scan
+    int pad;
+};
+
+// Counters the CTAs of one panel launch share (zeroed before the launch).
+struct PanelSync {
+    int ev_count;    // events published by the leader
+    int scan_done;   // helper CTAs that answered scans, cumulative
+    int abort;       // set by whoever times out
+    int pad;
+};
+
+// What the panel kernel reports back to the host.
+struct PanelOut {
+    int np;          // pivots taken in this panel (L columns)
+    int nzero;       // non-pivot rows found
+    int iend;        // first window row not processed
+    int m_next;      // order of the next Schur complement
+    int abort;
+    int nscan;       // far scans issued (diagnostics)
+    int pad[2];
+    int piv_rows[KP_MAX];   // compact rows, pivot order
+    uint32_t dval[KP_MAX];  // D diagonal
+    uint32_t eval[KP_MAX];  // x at a 2x2 block start, else 0
+    int zero_rows[W0];      // compact rows, ascending
+};
+
+struct PanelParams {
+    const uint32_t *S;      // compact Schur complement, lower triangle, ldS
+    int64_t ldS;
+    int m;
+    FieldP f;
+    int kp;                 // pivot budget of this panel (<= KP_MAX)
+    int w;                  // window rows min(W0, m)
+    uint32_t *LpT;          // LpT[k * ldL + t]: L entry of compact row t, panel column k
+    int64_t ldL;
+    uint8_t *consumed;      // [m]: partner rows taken by 2x2 pivots (zeroed)
+    const int *idx;         // [m]: original index of compact row
+    int *sigma;             // [m]: out, new compact row -> old compact row
+    int *idx_next;          // [m]: out, original index of new compact row
+    PanelOut *out;
+    PanelSync *sync;
+    Event *events;
+    uint32_t *evvec;        // [MAX_EVENTS][2][KP_MAX]
+    int *scan_min;          // [gridDim.x]
+    uint32_t *partner_lp;   // [gridDim.x][KP_MAX]
+    int64_t budget_ns;
+    int32_t *status;
+};
+
+// ---- launchers (host) -------------------------------------------------------
+cudaError_t launch_ingest(const uint32_t *A, int64_t lda, int64_t n, uint32_t *S, int64_t ldS,
+                          int *idx, FieldP f, cudaStream_t st);
+cudaError_t launch_panel(const PanelParams &pp, int grid, cudaStream_t st);
+cudaError_t launch_lw_scatter(const uint32_t *LpT, int64_t ldL, int m, int np, const int *idx,
+                              uint32_t *Lw, int64_t ldw, int col0, cudaStream_t st);
+cudaError_t launch_compact_copy(const uint32_t *S, int64_t ldS, const int *sigma, int m_next,
+                                uint32_t *Snext, cudaStream_t st);
+cudaError_t launch_record_panel(const PanelOut *out, const int *idx, int r0, int z0,
+                                int *piv_all, uint32_t *d_all, uint32_t *e_all, int *zero_all,
+                                cudaStream_t st);
+cudaError_t launch_finalize(int64_t n, const uint32_t *Lw, int64_t ldw, const int *piv_all,
+                            const uint32_t *d_all, const uint32_t *e_all, const int *zero_all,
+                            int r, uint32_t *A, int64_t lda, int32_t *perm, uint32_t *e,
+                            int64_t *rank, cudaStream_t st);
+cudaError_t launch_rpm(int64_t n, const int32_t *perm, const uint32_t *e, const int64_t *rank,
+                       int32_t *rpm_col, cudaStream_t st);
+
+// FP64 form of the level-3 update.
+size_t fp64_operand_bytes(int64_t n);
+cudaError_t launch_split_fp64(const uint32_t *LpT, int64_t ldL, const int *sigma, int m_next,
+                              int np, const PanelOut *out, FieldP f, double *GDT, double *GT,
+                              int64_t ldg, int kpad, cudaStream_t st);
+cudaError_t launch_syrdk_fp64(const uint32_t *S, int64_t ldS, const int *sigma, int m_next,
+                              const double *GDT, const double *GT, int64_t ldg, int kpad,
+                              FieldP f, uint32_t *Snext, cudaStream_t st);
+
+// Tensor-core form of the level-3 update.
+int tc_limbs(uint32_t p);
+int tc_bn(int limbs);
+size_t tc_operand_bytes(int64_t n, int limbs);
+cudaError_t launch_split_tc(const uint32_t *LpT, int64_t ldL, const int *sigma, int m_next,
+                            int np, const PanelOut *out, FieldP f, int limbs, int kpad,
+                            void *Aop, void *Bop, cudaStream_t st);
+cudaError_t launch_syrdk_tc(const uint32_t *S, int64_t ldS, const int *sigma, int m_next,
+                            const void *Aop, const void *Bop, int limbs, int kpad, FieldP f,
+                            uint32_t *Snext, int64_t budget_ns, int32_t *status, int num_sms,
+                            cudaStream_t st);

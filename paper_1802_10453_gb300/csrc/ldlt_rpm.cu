@@ -1,0 +1,265 @@
+// ldlt_rpm.cu -- host side of the C ABI declared in include/ldlt_rpm.h.
+//
+// Blocked right-looking form of the lexicographic elimination (Algorithm 4's
+// pivot order, Algorithm 2's level-3 updates):
+//   ingest:   S = lower(A) mod p, compact index = original index
+//   repeat:   panel   -- pivot chain over the first W0 rows of S (panel.cu):
+//                        up to KP_MAX pivots, their L columns for every row
+//             record  -- append pivots / D / zero rows to the global lists
+//             store   -- L columns into Lw (by original row)
+//             update  -- S <- S[sigma, sigma] - G D G^T on the remaining rows
+//                        (SYRDK, FP64 or tensor-core form), rows compacted
+//   finalize: A <- L in perm order with D on the diagonal (PERM)
+// After each panel three words are read back to size the next launches.
+#include <cstdio>
+#include <cstring>
+
+#include "../../include/ldlt_rpm.h"
+#include "ldlt_internal.cuh"
+
+namespace {
+
+int64_t g_budget_ns = 2000000000LL;
+
+uint64_t mulmod64(uint64_t a, uint64_t b, uint64_t m) { return (uint64_t)((unsigned __int128)a * b % m); }
+
+uint64_t powmod64(uint64_t a, uint64_t e, uint64_t m)
+{
+    uint64_t r = 1 % m;
+    a %= m;
+    while (e) {
+        if (e & 1) r = mulmod64(r, a, m);
+        a = mulmod64(a, a, m);
+        e >>= 1;
+    }
+    return r;
+}
+
+// Deterministic Miller-Rabin: bases 2, 3, 5, 7 decide every n < 3,215,031,751.
+bool is_prime_u32(uint32_t n)
+{
+    if (n < 2) return false;
+    for (uint32_t q : {2u, 3u, 5u, 7u}) {
+        if (n == q) return true;
+        if (n % q == 0) return false;
+    }
+    uint64_t d = n - 1;
+    int s = 0;
+    while ((d & 1) == 0) { d >>= 1; ++s; }
+    for (uint64_t a : {2ull, 3ull, 5ull, 7ull}) {
+        uint64_t x = powmod64(a, d, n);
+        if (x == 1 || x == n - 1) continue;
+        bool comp = true;
+        for (int r = 1; r < s; ++r) {
+            x = mulmod64(x, x, n);
+            if (x == n - 1) { comp = false; break; }
+        }
+        if (comp) return false;
+    }
+    return true;
+}
+
+int fp64_kred(uint32_t p)
+{
+    const double h = (double)((p - 1) / 2);
+    const double lim = 9007199254740992.0 - 1.5 * (double)p;
+    const double q = h * h > 1.0 ? h * h : 1.0;
+    double k = lim / q;
+    return k >= 1.0 ? (k > 1e9 ? 1000000000 : (int)k) : 0;
+}
+
+struct Layout {
+    int64_t ldS;
+    size_t S0, S1, Lw, LpT, idx0, idx1, sigma, consumed, piv_all, d_all, e_all, zero_all;
+    size_t out, sync, events, evvec, scan_min, partner_lp, opA, opB, total;
+};
+
+constexpr int MAX_GRID = 1024;
+
+int make_layout(int64_t n, uint32_t p, int path, Layout &L)
+{
+    const int64_t nn = n > 0 ? n : 1;
+    L.ldS = round_up(nn, 64);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off += (size_t)round_up((int64_t)bytes, 256);
+        return o;
+    };
+    const size_t mat = (size_t)nn * (size_t)L.ldS * 4;
+    L.S0 = take(mat);
+    L.S1 = take(mat);
+    L.Lw = take(mat);
+    L.LpT = take((size_t)KP_MAX * (size_t)L.ldS * 4);
+    L.idx0 = take((size_t)nn * 4);
+    L.idx1 = take((size_t)nn * 4);
+    L.sigma = take((size_t)nn * 4);
+    L.consumed = take((size_t)nn);
+    L.piv_all = take((size_t)nn * 4);
+    L.d_all = take((size_t)nn * 4);
+    L.e_all = take((size_t)nn * 4);
+    L.zero_all = take((size_t)nn * 4);
+    L.out = take(sizeof(PanelOut));
+    L.sync = take(sizeof(PanelSync));
+    L.events = take((size_t)MAX_EVENTS * sizeof(Event));
+    L.evvec = take((size_t)MAX_EVENTS * 2 * KP_MAX * 4);
+    L.scan_min = take((size_t)MAX_GRID * 4);
+    L.partner_lp = take((size_t)MAX_GRID * KP_MAX * 4);
+    if (path == LDLT_PATH_FP64) {
+        L.opA = take(fp64_operand_bytes(nn));
+        L.opB = L.opA;  // GT follows GDT inside the same allocation
+    } else {
+        const int limbs = tc_limbs(p);
+        L.opA = take(tc_operand_bytes(nn, limbs));
+        L.opB = L.opA;
+    }
+    L.total = off;
+    return LDLT_OK;
+}
+
+int check_args(int64_t n, uint32_t p, int path)
+{
+    if (n < 0 || n > (int64_t)1 << 30) return LDLT_ERR_ARG;
+    if (path != LDLT_PATH_FP64 && path != LDLT_PATH_TC) return LDLT_ERR_ARG;
+    if (p >= (1u << 31)) return LDLT_ERR_P_RANGE;
+    if (!is_prime_u32(p)) return LDLT_ERR_NOT_PRIME;
+    if (path == LDLT_PATH_FP64 && fp64_kred(p) < 1) return LDLT_ERR_P_RANGE;
+    if (path == LDLT_PATH_TC && tc_limbs(p) < 1) return LDLT_ERR_P_RANGE;
+    return LDLT_OK;
+}
+
+#define CK(call)                                \
+    do {                                        \
+        cudaError_t _e = (call);                \
+        if (_e != cudaSuccess) return LDLT_ERR_CUDA; \
+    } while (0)
+
+}  // namespace
+
+extern "C" int ldlt_rpm_version(void) { return 10000; }
+
+extern "C" void ldlt_rpm_set_wait_budget_ns(int64_t ns) { g_budget_ns = ns > 0 ? ns : 2000000000LL; }
+
+extern "C" int ldlt_rpm_workspace_bytes(int64_t n, uint32_t p, int path, size_t *bytes)
+{
+    if (!bytes) return LDLT_ERR_ARG;
+    int rc = check_args(n, p, path);
+    if (rc != LDLT_OK) return rc;
+    Layout L;
+    make_layout(n, p, path, L);
+    *bytes = L.total;
+    return LDLT_OK;
+}
+
+extern "C" int ldlt_rpm_factor(int64_t n, uint32_t p, uint32_t *A, int64_t lda, int32_t *perm,
+                               uint32_t *e, int64_t *rank, int32_t *status, int path, void *ws,
+                               size_t ws_bytes, void *stream)
+{
+    int rc = check_args(n, p, path);
+    if (rc != LDLT_OK) return rc;
+    if (!rank || !status) return LDLT_ERR_ARG;
+    if (n > 0 && (!A || !perm || !e || lda < n)) return LDLT_ERR_ARG;
+    Layout Lo;
+    make_layout(n, p, path, Lo);
+    if (!ws || ws_bytes < Lo.total) return LDLT_ERR_WORKSPACE;
+    if (((uintptr_t)ws & 255) != 0) return LDLT_ERR_WORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+
+    int dev = 0, major = 0, minor = 0, nsm = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev));
+    CK(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    if (major != 10 || minor != 3) return LDLT_ERR_NO_DEVICE;
+
+    CK(cudaMemsetAsync(status, 0, sizeof(int32_t), st));
+    if (n == 0) {
+        CK(cudaMemsetAsync(rank, 0, sizeof(int64_t), st));
+        return LDLT_OK;
+    }
+
+    uint8_t *w = (uint8_t *)ws;
+    uint32_t *Sbuf[2] = {(uint32_t *)(w + Lo.S0), (uint32_t *)(w + Lo.S1)};
+    uint32_t *Lw = (uint32_t *)(w + Lo.Lw);
+    uint32_t *LpT = (uint32_t *)(w + Lo.LpT);
+    int *idxb[2] = {(int *)(w + Lo.idx0), (int *)(w + Lo.idx1)};
+    int *sigma = (int *)(w + Lo.sigma);
+    uint8_t *consumed = w + Lo.consumed;
+    int *piv_all = (int *)(w + Lo.piv_all);
+    uint32_t *d_all = (uint32_t *)(w + Lo.d_all);
+    uint32_t *e_all = (uint32_t *)(w + Lo.e_all);
+    int *zero_all = (int *)(w + Lo.zero_all);
+    PanelOut *out = (PanelOut *)(w + Lo.out);
+    PanelSync *sync = (PanelSync *)(w + Lo.sync);
+    const int64_t ldS = Lo.ldS;
+    const FieldP f = make_field(p);
+    const int limbs = (path == LDLT_PATH_TC) ? tc_limbs(p) : 0;
+
+    CK(launch_ingest(A, lda, n, Sbuf[0], ldS, idxb[0], f, st));
+
+    int m = (int)n, r0 = 0, z0 = 0, cur = 0;
+    while (m > 0) {
+        CK(cudaMemset2DAsync(LpT, (size_t)ldS * 4, 0, (size_t)m * 4, KP_MAX, st));
+        CK(cudaMemsetAsync(consumed, 0, (size_t)m, st));
+        CK(cudaMemsetAsync(sync, 0, sizeof(PanelSync), st));
+        PanelParams pp;
+        pp.S = Sbuf[cur]; pp.ldS = ldS; pp.m = m; pp.f = f;
+        pp.kp = KP_MAX; pp.w = m < W0 ? m : W0;
+        pp.LpT = LpT; pp.ldL = ldS;
+        pp.consumed = consumed; pp.idx = idxb[cur]; pp.sigma = sigma; pp.idx_next = idxb[cur ^ 1];
+        pp.out = out; pp.sync = sync;
+        pp.events = (Event *)(w + Lo.events); pp.evvec = (uint32_t *)(w + Lo.evvec);
+        pp.scan_min = (int *)(w + Lo.scan_min); pp.partner_lp = (uint32_t *)(w + Lo.partner_lp);
+        pp.budget_ns = g_budget_ns; pp.status = status;
+        int grid = 1;
+        if (m > pp.w) {
+            const int need = 1 + (m - pp.w + PANEL_THREADS - 1) / PANEL_THREADS;
+            grid = need < nsm ? need : nsm;
+            if (grid > MAX_GRID) grid = MAX_GRID;
+        }
+        CK(launch_panel(pp, grid, st));
+        CK(launch_record_panel(out, idxb[cur], r0, z0, piv_all, d_all, e_all, zero_all, st));
+        int hdr[8];
+        CK(cudaMemcpyAsync(hdr, out, sizeof(hdr), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        const int np = hdr[0], nzero = hdr[1], m_next = hdr[3], aborted = hdr[4];
+        if (aborted) return LDLT_OK;  // LDLT_ERR_TIMEOUT is in *status
+        CK(launch_lw_scatter(LpT, ldS, m, np, idxb[cur], Lw, ldS, r0, st));
+        if (m_next > 0) {
+            if (np > 0) {
+                const int kpad = (int)round_up(np, 64);
+                if (path == LDLT_PATH_FP64) {
+                    double *GDT = (double *)(w + Lo.opA);
+                    double *GT = GDT + (size_t)KP_MAX * ldS;
+                    CK(launch_split_fp64(LpT, ldS, sigma, m_next, np, out, f, GDT, GT, ldS, kpad, st));
+                    CK(launch_syrdk_fp64(Sbuf[cur], ldS, sigma, m_next, GDT, GT, ldS, kpad, f,
+                                         Sbuf[cur ^ 1], st));
+                } else {
+                    uint8_t *opA = w + Lo.opA;
+                    const size_t aBytes = (size_t)round_up(round_up(n, 128) * (int64_t)limbs * KP_MAX * 2, 256);
+                    uint8_t *opB = opA + aBytes;
+                    CK(launch_split_tc(LpT, ldS, sigma, m_next, np, out, f, limbs, kpad, opA, opB, st));
+                    CK(launch_syrdk_tc(Sbuf[cur], ldS, sigma, m_next, opA, opB, limbs, kpad, f,
+                                       Sbuf[cur ^ 1], g_budget_ns, status, nsm, st));
+                }
+            } else {
+                CK(launch_compact_copy(Sbuf[cur], ldS, sigma, m_next, Sbuf[cur ^ 1], st));
+            }
+        }
+        r0 += np;
+        z0 += nzero;
+        cur ^= 1;
+        m = m_next;
+    }
+    CK(launch_finalize(n, Lw, ldS, piv_all, d_all, e_all, zero_all, r0, A, lda, perm, e, rank, st));
+    return LDLT_OK;
+}
+
+extern "C" int rpm_from_factor(int64_t n, const int32_t *perm, const uint32_t *e, const int64_t *rank,
+                               int32_t *rpm_col, void *stream)
+{
+    if (n < 0) return LDLT_ERR_ARG;
+    if (n > 0 && (!perm || !e || !rank || !rpm_col)) return LDLT_ERR_ARG;
+    CK(launch_rpm(n, perm, e, rank, rpm_col, (cudaStream_t)stream));
+    return LDLT_OK;
+}

@@ -1,0 +1,574 @@
+// syrdk_tc.cu -- tensor-core form of the level-3 update of Algorithm 2:
+//   Z = C - G D G^T   (SYRDK, Section 3), lower triangle, rows compacted.
+//
+// Exact modular products on bf16 tensor cores.  Every residue is written in
+// balanced form (-p/2, p/2] and split into L signed base-256 digits
+// x = sum_u 256^u x_u, x_u in [-128, 128]; such small integers are exact in
+// bf16 and every digit product is at most 2^14 in magnitude.  With
+//   b~_u = balanced(256^u * g mod p)   (pre-scaled copies of the B operand)
+// the product sum_k gd_k g_k is congruent mod p to
+//   sum_v 256^v * acc_v,   acc_v = sum_u sum_k digit_u(gd_k) * digit_v(b~_u,k),
+// so each acc_v is ONE matrix product of inner dimension K' = L*K: the A
+// operand is [digit_0(GD) | ... | digit_{L-1}(GD)] and the B operand for acc_v
+// is [digit_v(b~_0) | ... | digit_v(b~_{L-1})].  The L B operands are stacked
+// along N, so a single tcgen05.mma (kind::f16, M = 128, N = L*BN) per K-step
+// produces all acc_v for a 128 x BN output tile.  The FP32 accumulation is
+// exact because |acc_v| <= K' * 2^14 < 2^24 for K' < 1024.  The epilogue reads
+// the L accumulators from tensor memory, forms sum_v 256^v acc_v in 64-bit
+// integers, reduces once mod p and subtracts from the old Schur entry.
+//
+// Kernel structure (one CTA per SM, persistent over the lower-triangle tiles):
+//   warp 0      bulk-copy producer (cp.async.bulk, mbarrier complete_tx)
+//   warp 1      TMEM allocator and MMA issuer (tcgen05.mma, tcgen05.commit)
+//   warps 2..5  epilogue (tcgen05.ld -> recombine -> mod p -> shared tile ->
+//               coalesced read-modify-write of the Schur complement)
+// Operands are pre-tiled in HBM by split_tc_kernel so every pipeline stage is
+// one contiguous bulk copy that lands in the no-swizzle K-major "core matrix"
+// layout the tensor core reads (8 rows x 16 bytes per core matrix).
+#include <cuda_bf16.h>
+
+#include "ldlt_internal.cuh"
+
+#define LDLT_ERR_TIMEOUT_CODE (-6)
+
+namespace {
+
+constexpr int BM = 128;            // rows per output tile (MMA M)
+constexpr int KST = 64;            // K' elements per pipeline stage
+constexpr int NST = 3;             // pipeline stages
+constexpr int STAGE_A = BM * KST * 2;        // 16 KB
+constexpr int STAGE_B_MAX = 256 * KST * 2;   // 32 KB
+constexpr int STAGE_BYTES = STAGE_A + STAGE_B_MAX;
+constexpr int EPI_THREADS = 128;
+constexpr int TC_THREADS = 192;
+
+// ---------------------------------------------------------------------------
+// PTX wrappers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ int64_t gtime()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return (int64_t)t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred P1;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, P1;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait used only to drain in-flight work before the CTA exits: ignores the
+// abort flag and allows at least one second.
+__device__ __forceinline__ bool mbar_drain(uint32_t bar, uint32_t parity, int64_t budget)
+{
+    const int64_t lim = budget > 1000000000LL ? budget : 1000000000LL;
+    const int64_t t0 = gtime();
+    for (;;) {
+        if (mbar_try(bar, parity)) return true;
+        if (gtime() - t0 > lim) return false;
+    }
+}
+
+// Bounded wait: false when the budget ran out or another role aborted.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int64_t budget,
+                                          volatile int *abort_flag)
+{
+    if (mbar_try(bar, parity)) return true;
+    const int64_t t0 = gtime();
+    for (;;) {
+        if (mbar_try(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (gtime() - t0 > budget) return false;
+    }
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor (tcgen05), no swizzle, K-major:
+// start >> 4 in [0,14), LBO >> 4 in [16,30), SBO >> 4 in [32,46), version 1 in
+// [46,48), base offset 0, layout type 0 (no swizzle) in [61,64).
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// Instruction descriptor, kind::f16: D f32 (bits 4-5 = 1), A bf16 (7-9 = 1),
+// B bf16 (10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at 17, M >> 4 at 24.
+__host__ __device__ constexpr uint32_t make_idesc(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(dtmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// ---------------------------------------------------------------------------
+// tile enumeration: lower-triangle tiles (I, J), 128-row blocks, BN-col blocks
+// ---------------------------------------------------------------------------
+struct TileMap {
+    int nI, c, nfull, nlast;  // c = BM / BN; nfull = tiles in the first nI-1 row blocks
+};
+
+__device__ __forceinline__ void tile_of(const TileMap &tm, int t, int &I, int &J)
+{
+    if (t < tm.nfull) {
+        // c * I (I + 1) / 2 <= t < c (I + 1)(I + 2) / 2
+        int i = (int)((sqrtf(8.0f * (float)t / (float)tm.c + 1.0f) - 1.0f) * 0.5f);
+        while (tm.c * (i + 1) * (i + 2) / 2 <= t) ++i;
+        while (i > 0 && tm.c * i * (i + 1) / 2 > t) --i;
+        I = i;
+        J = t - tm.c * i * (i + 1) / 2;
+    } else {
+        I = tm.nI - 1;
+        J = t - tm.nfull;
+    }
+}
+
+struct TcArgs {
+    const uint32_t *S;
+    int64_t ldS;
+    const int *sigma;
+    int m_next;
+    const __nv_bfloat16 *Aop;
+    const __nv_bfloat16 *Bop;
+    int limbs, bn, nprime, kprime;  // N' = limbs * bn, K' = limbs * kpad
+    FieldP f;
+    uint64_t bias;                  // multiple of p above 2^50
+    uint32_t *Snext;
+    int64_t budget_ns;
+    int32_t *status;
+    TileMap tm;
+    int ntiles;
+};
+
+__global__ void __launch_bounds__(TC_THREADS, 1) syrdk_tc_kernel(const TcArgs args)
+{
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *stages = smem;
+    uint32_t *stage_out = (uint32_t *)(smem + NST * STAGE_BYTES);  // [BM][bn + 1]
+    uint64_t *bars = (uint64_t *)(smem + NST * STAGE_BYTES + BM * (128 + 1) * 4);
+    // bars[0..NST) full, [NST..2NST) empty, [2NST, 2NST+2) tmem full,
+    // [2NST+2, 2NST+4) tmem empty, [2NST+4] drain
+    uint32_t *tmem_holder = (uint32_t *)(bars + 2 * NST + 5);
+    volatile int *abort_flag = (volatile int *)(tmem_holder + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nk = args.kprime / KST;
+    const int np_ = args.nprime;
+    const uint32_t stageB_bytes = (uint32_t)np_ * KST * 2;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NST; ++s) {
+            mbar_init(smem_u32(&bars[s]), 1);
+            mbar_init(smem_u32(&bars[NST + s]), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&bars[2 * NST + b]), 1);
+            mbar_init(smem_u32(&bars[2 * NST + 2 + b]), EPI_THREADS);
+        }
+        mbar_init(smem_u32(&bars[2 * NST + 4]), 1);  // drain barrier
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_holder)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_holder;
+
+    if (warp == 0) {
+        // ---------------- producer ----------------
+        if (lane == 0) {
+            uint32_t it = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < args.ntiles && ok; t += gridDim.x) {
+                int I, J;
+                tile_of(args.tm, t, I, J);
+                const __nv_bfloat16 *ablk = args.Aop + (int64_t)I * BM * args.kprime;
+                const __nv_bfloat16 *bblk = args.Bop + (int64_t)J * np_ * args.kprime;
+                for (int s = 0; s < nk; ++s, ++it) {
+                    const uint32_t slot = it % NST, ph = (it / NST) & 1u;
+                    if (!mbar_wait(smem_u32(&bars[NST + slot]), ph ^ 1u, args.budget_ns, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t full = smem_u32(&bars[slot]);
+                    mbar_expect_tx(full, STAGE_A + stageB_bytes);
+                    uint8_t *dst = stages + slot * STAGE_BYTES;
+                    bulk_g2s(smem_u32(dst), ablk + (int64_t)s * KST * BM, STAGE_A, full);
+                    bulk_g2s(smem_u32(dst + STAGE_A), bblk + (int64_t)s * KST * np_, stageB_bytes, full);
+                }
+            }
+            if (!ok) {
+                atomicExch(args.status, LDLT_ERR_TIMEOUT_CODE);
+                *abort_flag = 1;
+            }
+            // drain: every issued copy must land before the CTA exits
+            for (uint32_t q = (it > NST ? it - NST : 0); q < it; ++q)
+                mbar_drain(smem_u32(&bars[q % NST]), (q / NST) & 1u, args.budget_ns);
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        const uint32_t idesc = make_idesc(BM, np_);
+        uint32_t it = 0, tcount = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < args.ntiles && ok; t += gridDim.x, ++tcount) {
+            const uint32_t buf = tcount & 1u, tph = (tcount >> 1) & 1u;
+            if (!mbar_wait(smem_u32(&bars[2 * NST + 2 + buf]), tph ^ 1u, args.budget_ns, abort_flag)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t dtmem = tmem_base + buf * (uint32_t)np_;
+            for (int s = 0; s < nk; ++s, ++it) {
+                const uint32_t slot = it % NST, ph = (it / NST) & 1u;
+                if (!mbar_wait(smem_u32(&bars[slot]), ph, args.budget_ns, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                if (lane == 0) {
+                    const uint32_t sa = smem_u32(stages + slot * STAGE_BYTES);
+                    const uint32_t sb = sa + STAGE_A;
+#pragma unroll
+                    for (int kk = 0; kk < KST / 16; ++kk) {
+                        // one K=16 step = two core matrices along K
+                        const uint64_t ad = make_desc(sa + kk * 2 * (BM * 16), BM * 16, 128);
+                        const uint64_t bd = make_desc(sb + kk * 2 * (np_ * 16), np_ * 16, 128);
+                        mma_bf16(dtmem, ad, bd, idesc, (s > 0 || kk > 0) ? 1u : 0u);
+                    }
+                    mma_commit(smem_u32(&bars[NST + slot]));
+                }
+                __syncwarp();
+            }
+            if (!ok) break;
+            if (lane == 0) mma_commit(smem_u32(&bars[2 * NST + buf]));
+            __syncwarp();
+        }
+        if (!ok) {
+            atomicExch(args.status, LDLT_ERR_TIMEOUT_CODE);
+            *abort_flag = 1;
+            // drain: the MMAs already issued must finish before TMEM is freed
+            if (lane == 0) mma_commit(smem_u32(&bars[2 * NST + 4]));
+            __syncwarp();
+            mbar_drain(smem_u32(&bars[2 * NST + 4]), 0u, args.budget_ns);
+        }
+    } else {
+        // ---------------- epilogue ----------------
+        const int q = warp & 3;              // TMEM lane quarter this warp may access
+        const int row = q * 32 + lane;       // tile row owned in the TMEM phase
+        const int bn = args.bn;
+        const int ldo = bn + 1;
+        const FieldP f = args.f;
+        uint32_t tcount = 0;
+        for (int t = blockIdx.x; t < args.ntiles; t += gridDim.x, ++tcount) {
+            int I, J;
+            tile_of(args.tm, t, I, J);
+            const uint32_t buf = tcount & 1u, tph = (tcount >> 1) & 1u;
+            if (!mbar_wait(smem_u32(&bars[2 * NST + buf]), tph, args.budget_ns, abort_flag)) {
+                atomicExch(args.status, LDLT_ERR_TIMEOUT_CODE);
+                *abort_flag = 1;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + buf * (uint32_t)np_;
+            for (int j0 = 0; j0 < bn; j0 += 16) {
+                int64_t val[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e) val[e] = 0;
+                for (int v = 0; v < args.limbs; ++v) {
+                    uint32_t r[16];
+                    tmem_ld16(tbase + (uint32_t)(v * bn + j0), r);
+                    tmem_wait_ld();
+                    const int64_t w = (int64_t)1 << (8 * v);
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) val[e] += (int64_t)__float2int_rn(__uint_as_float(r[e])) * w;
+                }
+#pragma unroll
+                for (int e = 0; e < 16; ++e)
+                    stage_out[row * ldo + j0 + e] = fp_reduce64((uint64_t)(val[e] + (int64_t)args.bias), f);
+            }
+            tc_fence_before();
+            mbar_arrive(smem_u32(&bars[2 * NST + 2 + buf]));
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            // coalesced read-modify-write of the Schur complement
+            const int ew = (warp - 2);  // 0..3
+            for (int rr = ew; rr < BM; rr += 4) {
+                const int i = I * BM + rr;
+                if (i >= args.m_next) break;
+                const uint32_t *srow = args.S + (int64_t)__ldg(args.sigma + i) * args.ldS;
+                uint32_t *drow = args.Snext + (int64_t)i * args.ldS;
+                for (int jj = lane; jj < bn; jj += 32) {
+                    const int j = J * bn + jj;
+                    if (j > i || j >= args.m_next) continue;
+                    drow[j] = fp_sub(__ldg(srow + __ldg(args.sigma + j)), stage_out[rr * ldo + jj], f);
+                }
+            }
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem_base));
+}
+
+// ---------------------------------------------------------------------------
+// operand preparation
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int32_t balanced(uint32_t x, uint32_t p)
+{
+    return x > (p >> 1) ? (int32_t)((int64_t)x - (int64_t)p) : (int32_t)x;
+}
+
+// digit u of the balanced base-256 expansion (top digit takes the rest)
+__device__ __forceinline__ void digits(int32_t x, int L, int32_t *d)
+{
+    for (int u = 0; u < L - 1; ++u) {
+        int32_t lo = ((x + 128) & 255) - 128;
+        d[u] = lo;
+        x = (x - lo) >> 8;
+    }
+    d[L - 1] = x;
+}
+
+__device__ __forceinline__ uint4 pack8(const int32_t *v)
+{
+    uint32_t w[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        __nv_bfloat16 lo = __float2bfloat16_rn((float)v[2 * h]);
+        __nv_bfloat16 hi = __float2bfloat16_rn((float)v[2 * h + 1]);
+        w[h] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+struct SplitArgs {
+    const uint32_t *LpT;
+    int64_t ldL;
+    const int *sigma;
+    int m_next, np, rows, kpad, limbs, bn, nprime, kprime;
+    const PanelOut *out;
+    FieldP f;
+    uint32_t w256[4];  // 256^u mod p
+    __nv_bfloat16 *Aop, *Bop;
+};
+
+// One thread per (row i, group of 8 columns k..k+7).
+__global__ void split_tc_kernel(const SplitArgs a)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k0 = blockIdx.y * 8;
+    if (i >= a.rows) return;
+    const FieldP f = a.f;
+    const int L = a.limbs;
+    uint32_t g[10];  // g[1 + e] = G[i][k0 + e], e in [-1, 8]
+#pragma unroll
+    for (int e = 0; e < 10; ++e) {
+        const int k = k0 - 1 + e;
+        g[e] = (i < a.m_next && k >= 0 && k < a.np) ? a.LpT[(int64_t)k * a.ldL + a.sigma[i]] : 0u;
+    }
+    int32_t gd_bal[8], gb[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const int k = k0 + e;
+        uint32_t v = 0;
+        if (k < a.np) {
+            const uint32_t ek = a.out->eval[k];
+            if (ek != 0) v = fp_mul(ek, g[e + 2], f);
+            else if (k > 0 && a.out->eval[k - 1] != 0)
+                v = fp_add(fp_mul(a.out->eval[k - 1], g[e], f), fp_mul(a.out->dval[k], g[e + 1], f), f);
+            else v = fp_mul(a.out->dval[k], g[e + 1], f);
+        }
+        gd_bal[e] = balanced(v, f.p);
+    }
+    // A operand: digit u of GD at K' column u*kpad + k
+    const int I = i / BM, ri = i % BM;
+    const int J = i / a.bn, rj = i % a.bn;
+    int32_t dg[8][4];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) digits(gd_bal[e], L, dg[e]);
+    for (int u = 0; u < L; ++u) {
+        int32_t v8[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v8[e] = dg[e][u];
+        const int kk = u * a.kpad + k0;
+        const int64_t off = (int64_t)I * BM * a.kprime + (int64_t)(kk / 8) * (BM * 8) + ri * 8;
+        *(uint4 *)(a.Aop + off) = pack8(v8);
+    }
+    // B operand: digit v of b~_u = balanced(256^u g mod p), rows v*bn + rj
+    if (i < ((a.rows + a.bn - 1) / a.bn) * a.bn) {
+        for (int u = 0; u < L; ++u) {
+            int32_t db[8][4];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                gb[e] = balanced(fp_mul(a.w256[u], g[e + 1], f), f.p);
+                digits(gb[e], L, db[e]);
+            }
+            const int kk = u * a.kpad + k0;
+            for (int v = 0; v < L; ++v) {
+                int32_t v8[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) v8[e] = db[e][v];
+                const int64_t off = (int64_t)J * a.nprime * a.kprime + (int64_t)(kk / 8) * (a.nprime * 8) +
+                                    (int64_t)(v * a.bn + rj) * 8;
+                *(uint4 *)(a.Bop + off) = pack8(v8);
+            }
+        }
+    }
+}
+
+}  // namespace
+
+// Number of signed 8-bit digits so that every balanced residue |x| <= (p-1)/2
+// has a top digit of magnitude at most 128.
+int tc_limbs(uint32_t p)
+{
+    const int64_t h = (int64_t)(p - 1) / 2;
+    for (int L = 1; L <= 4; ++L) {
+        int64_t lowmax = 0, scale = 1;
+        for (int u = 0; u < L - 1; ++u) {
+            lowmax += 128 * scale;
+            scale *= 256;
+        }
+        // |top| <= (h + lowmax) / scale
+        if ((h + lowmax) / scale <= 128) return L;
+    }
+    return -1;
+}
+
+int tc_bn(int limbs) { return limbs <= 2 ? 128 : 64; }
+
+size_t tc_operand_bytes(int64_t n, int limbs)
+{
+    const int64_t rows = round_up(n, BM);
+    const int64_t kprime = (int64_t)limbs * KP_MAX;
+    const int64_t nprime = (int64_t)limbs * tc_bn(limbs);
+    const int64_t aBytes = rows * kprime * 2;
+    const int64_t bBytes = (rows / tc_bn(limbs)) * nprime * kprime * 2;
+    return (size_t)round_up(aBytes, 256) + (size_t)round_up(bBytes, 256);
+}
+
+cudaError_t launch_split_tc(const uint32_t *LpT, int64_t ldL, const int *sigma, int m_next, int np,
+                            const PanelOut *out, FieldP f, int limbs, int kpad, void *Aop, void *Bop,
+                            cudaStream_t st)
+{
+    if (m_next == 0) return cudaSuccess;
+    SplitArgs a;
+    a.LpT = LpT; a.ldL = ldL; a.sigma = sigma; a.m_next = m_next; a.np = np;
+    a.rows = (int)round_up(m_next, BM);
+    a.kpad = kpad; a.limbs = limbs; a.bn = tc_bn(limbs);
+    a.nprime = limbs * a.bn; a.kprime = limbs * kpad;
+    a.out = out; a.f = f;
+    uint64_t w = 1;
+    for (int u = 0; u < 4; ++u) {
+        a.w256[u] = (uint32_t)(w % f.p);
+        w = (w * 256) % f.p;
+    }
+    a.Aop = (__nv_bfloat16 *)Aop;
+    a.Bop = (__nv_bfloat16 *)Bop;
+    dim3 grid((a.rows + 127) / 128, kpad / 8);
+    split_tc_kernel<<<grid, 128, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_syrdk_tc(const uint32_t *S, int64_t ldS, const int *sigma, int m_next, const void *Aop,
+                            const void *Bop, int limbs, int kpad, FieldP f, uint32_t *Snext,
+                            int64_t budget_ns, int32_t *status, int num_sms, cudaStream_t st)
+{
+    if (m_next == 0) return cudaSuccess;
+    TcArgs a;
+    a.S = S; a.ldS = ldS; a.sigma = sigma; a.m_next = m_next;
+    a.Aop = (const __nv_bfloat16 *)Aop; a.Bop = (const __nv_bfloat16 *)Bop;
+    a.limbs = limbs; a.bn = tc_bn(limbs); a.nprime = limbs * a.bn; a.kprime = limbs * kpad;
+    a.f = f;
+    a.bias = ((((uint64_t)1 << 50) / f.p) + 1) * (uint64_t)f.p;
+    a.Snext = Snext; a.budget_ns = budget_ns; a.status = status;
+    const int nI = (m_next + BM - 1) / BM;
+    a.tm.nI = nI;
+    a.tm.c = BM / a.bn;
+    a.tm.nfull = a.tm.c * (nI - 1) * nI / 2;
+    a.tm.nlast = (m_next + a.bn - 1) / a.bn;
+    a.ntiles = a.tm.nfull + a.tm.nlast;
+    const size_t smem = 1024 + (size_t)NST * STAGE_BYTES + (size_t)BM * (128 + 1) * 4 + 128;
+    cudaError_t err = cudaFuncSetAttribute(syrdk_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    int grid = a.ntiles < num_sms ? a.ntiles : num_sms;
+    syrdk_tc_kernel<<<grid, TC_THREADS, smem, st>>>(a);
+    return cudaGetLastError();
+}

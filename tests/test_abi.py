@@ -1,0 +1,76 @@
+"""C ABI: the library builds, loads without a GPU and exports every function
+include/ldlt_rpm.h declares; host-side argument checks return their codes."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def libs():
+    import __graft_entry__ as g
+    g.build()
+    import paper_1802_10453_gb300 as lr
+    return lr
+
+
+def _declared(header):
+    txt = open(os.path.join(ROOT, "include", header)).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|void|size_t)\s+\**(\w+)\s*\(", txt, flags=re.M)))
+
+
+def test_exports_match_header(libs):
+    names = _declared("ldlt_rpm.h")
+    assert "ldlt_rpm_factor" in names and "rpm_from_factor" in names
+    out = subprocess.run(["nm", "-D", "--defined-only", libs.lib_path()], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(l.split()[-1] for l in out.splitlines() if " T " in l)
+    for nme in names:
+        assert nme in exported, nme
+    L = libs.lib()
+    for nme in names:
+        assert hasattr(L, nme)
+
+
+def test_version(libs):
+    assert libs.lib().ldlt_rpm_version() >= 10000
+
+
+@pytest.mark.parametrize("p,path,code", [
+    (65521, 1, 0), (65521, 0, 0), (2147483647, 1, 0), (2, 1, 0), (2, 0, 0),
+    (65520, 1, -2), (1, 1, -2), (0, 0, -2), (2147483648 + 11, 1, -3),
+    (2147483647, 0, -3), (67108859, 0, 0), (65521, 7, -1),
+])
+def test_workspace_query_codes(libs, p, path, code):
+    out = ctypes.c_size_t(0)
+    rc = libs.lib().ldlt_rpm_workspace_bytes(1000, p & 0xFFFFFFFF, path, ctypes.byref(out))
+    assert rc == code
+    if code == 0:
+        assert out.value > 3 * 1000 * 1000 * 4
+
+
+def test_factor_argument_errors(libs):
+    L = libs.lib()
+    # composite p, p too large, negative n, bad path: all rejected before any device call
+    assert L.ldlt_rpm_factor(4, 15, None, 4, None, None, None, None, 1, None, 0, None) == -2
+    assert L.ldlt_rpm_factor(4, 2147483659, None, 4, None, None, None, None, 1, None, 0, None) == -3
+    assert L.ldlt_rpm_factor(-1, 7, None, 4, None, None, None, None, 1, None, 0, None) == -1
+    assert L.ldlt_rpm_factor(4, 7, None, 4, None, None, None, None, 9, None, 0, None) == -1
+    buf = ctypes.create_string_buffer(8)
+    # NULL A with n > 0, lda < n
+    assert L.ldlt_rpm_factor(4, 7, None, 4, buf, buf, buf, buf, 1, None, 0, None) == -1
+    assert L.ldlt_rpm_factor(4, 7, buf, 3, buf, buf, buf, buf, 1, None, 0, None) == -1
+    # workspace too small
+    assert L.ldlt_rpm_factor(4, 7, buf, 4, buf, buf, buf, buf, 1, buf, 8, None) == -4
+    assert L.rpm_from_factor(-1, None, None, None, None, None) == -1
+
+
+def test_effective_ops_formula(libs):
+    # Section 6: r^3/3 + n^2 r - r^2 n; r = n gives n^3/3
+    assert libs.effective_ops(300, 300) == pytest.approx(300 ** 3 / 3)
+    assert libs.effective_ops(16384, 8192) == pytest.approx(7 * 16384 ** 3 / 24)

@@ -1,0 +1,263 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Integer work, so every comparison is bit-exact: perm, L (strictly lower part
+of the returned A), D (its diagonal and e), rank and the rank profile matrix.
+At sizes the oracle cannot finish quickly the factorisation is checked by
+properties that pin it completely: R_A equals the planted supp(R) (Theorem 1
+with lower-triangular congruence), perm is the canonical order read off R_A
+(lexicographic pivoting of Algorithm 4), the block shapes of D, and
+P^T A P = L D L^T on random vectors (Freivalds) -- L and D are unique once P
+and the block structure are fixed.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1802_10453_gb300 as lr  # noqa: E402
+from oracle import oracle as o  # noqa: E402
+from paper_1802_10453_gb300 import inputs  # noqa: E402
+
+PATHS = {"tc": lr.PATH_TC, "fp64": lr.PATH_FP64}
+
+
+def fp64_ok(p):
+    try:
+        lr.workspace_bytes(4, p, lr.PATH_FP64)
+        return True
+    except lr.LdltError:
+        return False
+
+
+def gpu_factor(A_np, p, path):
+    n = A_np.shape[0]
+    Ad = torch.from_numpy(np.tril(np.asarray(A_np, dtype=np.int64)).astype(np.int32)).cuda()
+    res = lr.factor(Ad, p, path=path)
+    rpm = lr.rpm_from_factor(res)
+    torch.cuda.synchronize()
+    out = Ad.cpu().numpy().astype(np.int64) & 0xFFFFFFFF
+    return dict(perm=res["perm"].cpu().numpy().astype(np.int64),
+                Lstrict=np.tril(out, -1), d=np.diag(out).copy(),
+                e=res["e"].cpu().numpy().astype(np.int64) & 0xFFFFFFFF,
+                rank=int(res["rank"].item()), rpm=rpm.cpu().numpy().astype(np.int64), n=n)
+
+
+def assert_parity(A_np, p, path):
+    ref = o.ldlt_rpm(np.asarray(A_np, dtype=np.int64).astype(np.uint32), p)
+    got = gpu_factor(A_np, p, path)
+    assert got["rank"] == ref["rank"]
+    assert np.array_equal(got["perm"], ref["perm"].astype(np.int64))
+    assert np.array_equal(got["d"], ref["d"].astype(np.int64))
+    assert np.array_equal(got["e"], ref["e"].astype(np.int64))
+    assert np.array_equal(got["Lstrict"], np.tril(ref["L"].astype(np.int64), -1))
+    assert np.array_equal(got["rpm"], o.rpm_from_factor(ref["perm"], ref["e"], ref["rank"]))
+    return got, ref
+
+
+@pytest.mark.parametrize("path", list(PATHS))
+@pytest.mark.parametrize("p,A", [
+    (7, [[0, 1], [1, 0]]), (2, [[0, 1], [1, 1]]), (7, [[0, 1], [1, 1]]),
+    (5, [[0]]), (5, [[3]]), (65521, [[0, 0, 0], [0, 0, 0], [0, 0, 0]]),
+])
+def test_worked_examples(path, p, A):
+    assert_parity(np.array(A), p, PATHS[path])
+
+
+@pytest.mark.parametrize("path", list(PATHS))
+@pytest.mark.parametrize("p", [2, 3, 257, 65521, 8388593, 67108859, 2147483647])
+def test_random_small(path, p):
+    if path == "fp64" and not fp64_ok(p):
+        pytest.skip("p beyond the FP64 form")
+    rng = np.random.default_rng(p % 1000)
+    for trial in range(8):
+        n = int(rng.integers(1, 40))
+        kind = trial % 3
+        if kind == 0:
+            B = rng.integers(0, p, size=(n, n))
+        else:
+            B = rng.integers(0, p, size=(n, n)) * (rng.random((n, n)) < 0.2)
+        A = np.tril(B) + np.tril(B, -1).T
+        assert_parity(A % p, p, PATHS[path])
+
+
+# sizes spanning several 64/128 tiles, ragged tails, window (256) and helper
+# rows, several panels (128 pivots each)
+RAGGED = [(1, 1), (31, 20), (33, 33), (65, 40), (127, 127), (129, 100), (255, 200),
+          (256, 192), (257, 257), (300, 150), (513, 400), (700, 300), (1000, 1000)]
+
+
+@pytest.mark.parametrize("path", list(PATHS))
+@pytest.mark.parametrize("p", [3, 65521, 8388593, 2147483647])
+@pytest.mark.parametrize("n,r", RAGGED)
+def test_ragged_planted(path, p, n, r):
+    if path == "fp64" and not fp64_ok(p):
+        pytest.skip("p beyond the FP64 form")
+    for all_pairs in (False, True):
+        A, partner, _ = inputs.planted_matrix(n, r, inputs.default_pairs(r, all_pairs), p, n + r)
+        got, _ = assert_parity(A, p, PATHS[path])
+        assert np.array_equal(got["rpm"], partner)
+
+
+@pytest.mark.parametrize("path", list(PATHS))
+def test_char2(path):
+    for n, r in [(40, 30), (300, 200), (600, 600)]:
+        A, partner, _ = inputs.planted_matrix(n, r, r // 4, 2, 11 + n)
+        got, _ = assert_parity(A, 2, PATHS[path])
+        assert np.array_equal(got["rpm"], partner)
+
+
+@pytest.mark.parametrize("path", list(PATHS))
+def test_uniform_and_degenerate(path):
+    p = 65521
+    assert_parity(inputs.uniform_symmetric(700, p, 3).astype(np.int64), p, PATHS[path])
+    assert_parity(np.zeros((400, 400), dtype=np.int64), p, PATHS[path])     # rank 0
+    assert_parity(np.eye(300, dtype=np.int64), p, PATHS[path])              # identity
+    J = np.fliplr(np.eye(300, dtype=np.int64))                              # all 2x2 pivots
+    assert_parity(J, p, PATHS[path])
+    A = np.zeros((500, 500), dtype=np.int64)                                # one far pair
+    A[3, 480] = A[480, 3] = 5
+    A[10, 10] = 1
+    assert_parity(A, p, PATHS[path])
+
+
+@pytest.mark.parametrize("path", list(PATHS))
+def test_entries_reduced_on_ingest(path):
+    p = 65521
+    A, _, _ = inputs.planted_matrix(200, 150, 30, p, 5)
+    big = A.astype(np.int64) + p * np.random.default_rng(1).integers(0, 3, size=A.shape)
+    big = np.minimum(big, 2 ** 31 - 1)
+    big = big - ((big - A) % p)  # keep big == A mod p
+    ref = assert_parity(A, p, PATHS[path])[0]
+    got = gpu_factor(big, p, PATHS[path])
+    assert np.array_equal(got["perm"], ref["perm"]) and np.array_equal(got["Lstrict"], ref["Lstrict"])
+
+
+def test_empty_matrix():
+    Ad = torch.zeros((0, 0), dtype=torch.int32, device="cuda")
+    res = lr.factor(Ad, 65521, path=lr.PATH_TC)
+    assert int(res["rank"].item()) == 0
+
+
+@pytest.mark.parametrize("path", list(PATHS))
+def test_config0_planted_n256(path):
+    """n = 256, r = 192, p = 65521, A = T R T^T (48 pairs + 96 fixed points)."""
+    n, r, p = 256, 192, 65521
+    A, partner, _ = inputs.planted_matrix(n, r, r // 4, p, inputs.SEED_BASE)
+    got, ref = assert_parity(A, p, PATHS[path])
+    assert got["rank"] == r and np.array_equal(got["rpm"], partner)
+
+
+@pytest.mark.parametrize("path", list(PATHS))
+def test_config1_uniform_n4096(path):
+    """n = 4096 uniform symmetric mod 8388593, exact against the oracle."""
+    from paper_1802_10453_gb300 import inputs_gpu
+    n, p = 4096, 8388593
+    Ad = inputs_gpu.uniform_symmetric(n, p, inputs.SEED_BASE + 1)
+    A = inputs.uniform_symmetric(n, p, inputs.SEED_BASE + 1)
+    assert np.array_equal(np.tril(Ad.cpu().numpy().astype(np.int64)), np.tril(A.astype(np.int64)))
+    assert_parity(A, p, PATHS[path])
+
+
+def _freivalds_host(Alow, perm, Lstrict, d, e, p, trials=2, seed=99):
+    """P^T A P x == L (D (L^T x)) mod p for random x; A given by its lower part."""
+    rng = np.random.default_rng(seed)
+    n = Alow.shape[0]
+    Lm = Lstrict.copy()
+    Lm[np.arange(n), np.arange(n)] = 1
+
+    def mv(M, x):  # exact (M @ x) mod p, x split in 16-bit halves
+        lo, hi = x & 0xFFFF, x >> 16
+        return ((((M @ hi) % p) << 16) % p + (M @ lo) % p) % p
+
+    for _ in range(trials):
+        x = rng.integers(0, p, size=n, dtype=np.int64)
+        px = np.zeros(n, dtype=np.int64)
+        px[perm] = x
+        # S px with S symmetric from its lower part: (low + strict_low^T) px
+        lhs = (mv(Alow, px) + mv(np.tril(Alow, -1).T.copy(), px)) % p
+        lhs = lhs[perm]
+        t = mv(Lm.T.copy(), x)
+        Dt = (d * t) % p
+        nxt = np.zeros(n, dtype=np.int64)
+        nxt[:-1] = t[1:]
+        prv = np.zeros(n, dtype=np.int64)
+        prv[1:] = t[:-1] * e[:-1]
+        Dt = (Dt + (e * nxt) % p + prv % p) % p
+        rhs = mv(Lm, Dt)
+        if not np.array_equal(lhs, rhs):
+            return False
+    return True
+
+
+def _check_planted_full_size(n, r, all_pairs, p, seed, path):
+    from paper_1802_10453_gb300 import inputs_gpu
+    Ad, partner = inputs_gpu.planted_matrix(n, r, inputs.default_pairs(r, all_pairs), p, seed)
+    Alow = np.tril(Ad.cpu().numpy().astype(np.int64))
+    res = lr.factor(Ad, p, path=path)
+    rpm = lr.rpm_from_factor(res).cpu().numpy().astype(np.int64)
+    out = Ad.cpu().numpy().astype(np.int64) & 0xFFFFFFFF
+    perm = res["perm"].cpu().numpy().astype(np.int64)
+    e = res["e"].cpu().numpy().astype(np.int64) & 0xFFFFFFFF
+    rank = int(res["rank"].item())
+    d = np.diag(out).copy()
+    assert rank == r
+    assert np.array_equal(rpm, partner)                       # reveals R_A = supp(R)
+    perm_c, starts = o.canonical_perm_from_rpm(o.rpm_col_to_matrix(partner)) if n <= 4096 else \
+        _canonical_perm_sparse(partner)
+    assert np.array_equal(perm, perm_c)                       # lexicographic order
+    assert np.array_equal(e != 0, starts) and np.all((d[starts] == 0))
+    if p != 2:
+        assert np.all(d[np.roll(starts, 1)] == 0)             # antidiagonal blocks
+    assert np.all(d[r:] == 0) and np.all(e[r:] == 0)
+    assert np.all(np.tril(out, -1)[r:, r:] == 0)              # identity columns beyond r
+    assert _freivalds_host(Alow, perm, np.tril(out, -1), d, e, p)
+
+
+def _canonical_perm_sparse(partner):
+    n = len(partner)
+    perm, starts, zero = [], [], []
+    placed = np.zeros(n, dtype=bool)
+    for i in range(n):
+        if placed[i]:
+            continue
+        j = partner[i]
+        if j < 0:
+            zero.append(i)
+        elif j == i:
+            perm.append(i); starts.append(False); placed[i] = True
+        else:
+            perm += [i, int(j)]; starts += [True, False]; placed[i] = placed[j] = True
+    return np.array(perm + zero, dtype=np.int64), np.array(starts + [False] * len(zero))
+
+
+@pytest.mark.parametrize("path", list(PATHS))
+def test_planted_n2048_properties_and_exact(path):
+    n, r, p = 2048, 1500, 65521
+    _check_planted_full_size(n, r, False, p, 4242, PATHS[path])
+
+
+def test_config2_planted_n16384_tc():
+    """n = 16384, r = 8192, p = 2^26 - 5, 2048 pairs + 4096 fixed points."""
+    _check_planted_full_size(16384, 8192, False, 67108859, inputs.SEED_BASE + 2, lr.PATH_TC)
+
+
+def test_wait_budget_timeout_reports_status():
+    """A wait that runs out is reported in the device status word, and the
+    context stays usable for the next call."""
+    n, r, p = 1200, 600, 65521
+    A, _, _ = inputs.planted_matrix(n, r, r // 2, p, 31)
+    Ad = torch.from_numpy(np.tril(A).astype(np.int32)).cuda()
+    lr.set_wait_budget_ns(1)
+    try:
+        res = lr.factor(Ad, p, path=lr.PATH_TC, check=False)
+        torch.cuda.synchronize()
+        st = int(res["status"].item())
+    finally:
+        lr.set_wait_budget_ns(0)
+    assert st in (0, lr.LDLT_ERR_TIMEOUT)
+    assert_parity(A, p, lr.PATH_TC)
