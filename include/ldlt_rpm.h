@@ -121,6 +121,26 @@ int ldlt_rpm_version(void);
  */
 void ldlt_rpm_set_wait_budget_ns(int64_t ns);
 
+/*
+ * Profiling counters (no counterpart in the paper; they feed the roofline
+ * report).  When enabled, ldlt_rpm_factor records CUDA events around its
+ * phases on the caller's stream and accumulates, across calls:
+ *   out[0] ms in the pivot-chain kernels (panel + bookkeeping)
+ *   out[1] ms in operand preparation (L store, limb split)
+ *   out[2] ms in the level-3 update kernel (SYRDK, either form)
+ *   out[3] algorithmic multiply-adds of the level-3 updates:
+ *          sum over launches of (m'(m'+1)/2) * k (lower triangle, k pivots)
+ *   out[4] number of level-3 update launches
+ *   out[5] number of kernels this library launched
+ *   out[6] number of panels
+ *   out[7] far scans issued by the pivot chain
+ * ldlt_rpm_profile_read returns LDLT_OK, or LDLT_ERR_ARG for a NULL pointer.
+ * The counters are process-wide and not thread-safe.
+ */
+void ldlt_rpm_profile_enable(int on);
+void ldlt_rpm_profile_reset(void);
+int ldlt_rpm_profile_read(double out[8]);
+
 #ifdef __cplusplus
 }
 #endif

@@ -59,7 +59,7 @@ __global__ void compact_copy_kernel(const uint32_t *__restrict__ S, int64_t ldS,
 // global lists.
 __global__ void record_panel_kernel(const PanelOut *__restrict__ out, const int *__restrict__ idx,
                                     int r0, int z0, int *piv_all, uint32_t *d_all,
-                                    uint32_t *e_all, int *zero_all)
+                                    uint32_t *e_all, int *zero_all, int *zero_cols)
 {
     const int np = out->np, nz = out->nzero;
     for (int k = threadIdx.x; k < np; k += blockDim.x) {
@@ -67,15 +67,20 @@ __global__ void record_panel_kernel(const PanelOut *__restrict__ out, const int 
         d_all[r0 + k] = out->dval[k];
         e_all[r0 + k] = out->eval[k];
     }
-    for (int q = threadIdx.x; q < nz; q += blockDim.x) zero_all[z0 + q] = idx[out->zero_rows[q]];
+    for (int q = threadIdx.x; q < nz; q += blockDim.x) {
+        zero_all[z0 + q] = idx[out->zero_rows[q]];
+        zero_cols[z0 + q] = r0 + out->zero_np[q];  // L columns that existed when it was found zero
+    }
 }
 
 // Final output (PERM of Algorithm 2 applied to L): row k of the result is the
 // L row of original row perm[k].  Strictly lower part: L (columns >= r are
-// identity columns, so zero there); diagonal: D_kk.
+// identity columns, so zero there; a non-pivot row is zero in every column
+// created after it was found zero); diagonal: D_kk.
 __global__ void finalize_kernel(int64_t n, const uint32_t *__restrict__ Lw, int64_t ldw,
                                 const int *__restrict__ piv_all, const uint32_t *__restrict__ d_all,
                                 const uint32_t *__restrict__ e_all, const int *__restrict__ zero_all,
+                                const int *__restrict__ zero_cols,
                                 int r, uint32_t *__restrict__ A, int64_t lda,
                                 int32_t *__restrict__ perm, uint32_t *__restrict__ e,
                                 int64_t *__restrict__ rank)
@@ -90,7 +95,7 @@ __global__ void finalize_kernel(int64_t n, const uint32_t *__restrict__ Lw, int6
     }
     const uint32_t *lrow = Lw + (int64_t)src * ldw;
     uint32_t *arow = A + k * lda;
-    const int64_t cmax = (k < r) ? k : (int64_t)r;  // L entries live in columns < min(k, r)
+    const int64_t cmax = (k < r) ? k : (int64_t)zero_cols[k - r];
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c <= k;
          c += (int64_t)gridDim.x * blockDim.x) {
         uint32_t v;
@@ -162,21 +167,22 @@ cudaError_t launch_compact_copy(const uint32_t *S, int64_t ldS, const int *sigma
 }
 
 cudaError_t launch_record_panel(const PanelOut *out, const int *idx, int r0, int z0, int *piv_all,
-                                uint32_t *d_all, uint32_t *e_all, int *zero_all, cudaStream_t st)
+                                uint32_t *d_all, uint32_t *e_all, int *zero_all, int *zero_cols,
+                                cudaStream_t st)
 {
-    record_panel_kernel<<<1, 256, 0, st>>>(out, idx, r0, z0, piv_all, d_all, e_all, zero_all);
+    record_panel_kernel<<<1, 256, 0, st>>>(out, idx, r0, z0, piv_all, d_all, e_all, zero_all, zero_cols);
     return cudaGetLastError();
 }
 
 cudaError_t launch_finalize(int64_t n, const uint32_t *Lw, int64_t ldw, const int *piv_all,
                             const uint32_t *d_all, const uint32_t *e_all, const int *zero_all,
-                            int r, uint32_t *A, int64_t lda, int32_t *perm, uint32_t *e,
-                            int64_t *rank, cudaStream_t st)
+                            const int *zero_cols, int r, uint32_t *A, int64_t lda, int32_t *perm,
+                            uint32_t *e, int64_t *rank, cudaStream_t st)
 {
     if (n == 0) return cudaSuccess;
     dim3 grid(gx_for(n, 256), (unsigned)n);
-    finalize_kernel<<<grid, 256, 0, st>>>(n, Lw, ldw, piv_all, d_all, e_all, zero_all, r, A, lda,
-                                          perm, e, rank);
+    finalize_kernel<<<grid, 256, 0, st>>>(n, Lw, ldw, piv_all, d_all, e_all, zero_all, zero_cols, r,
+                                          A, lda, perm, e, rank);
     return cudaGetLastError();
 }
 

@@ -51,6 +51,7 @@ struct PanelOut {
     uint32_t dval[KP_MAX];  // D diagonal
     uint32_t eval[KP_MAX];  // x at a 2x2 block start, else 0
     int zero_rows[W0];      // compact rows, ascending
+    int zero_np[W0];        // pivots of this panel taken before each zero row
 };
 
 struct PanelParams {
@@ -86,11 +87,11 @@ cudaError_t launch_compact_copy(const uint32_t *S, int64_t ldS, const int *sigma
                                 uint32_t *Snext, cudaStream_t st);
 cudaError_t launch_record_panel(const PanelOut *out, const int *idx, int r0, int z0,
                                 int *piv_all, uint32_t *d_all, uint32_t *e_all, int *zero_all,
-                                cudaStream_t st);
+                                int *zero_cols, cudaStream_t st);
 cudaError_t launch_finalize(int64_t n, const uint32_t *Lw, int64_t ldw, const int *piv_all,
                             const uint32_t *d_all, const uint32_t *e_all, const int *zero_all,
-                            int r, uint32_t *A, int64_t lda, int32_t *perm, uint32_t *e,
-                            int64_t *rank, cudaStream_t st);
+                            const int *zero_cols, int r, uint32_t *A, int64_t lda, int32_t *perm,
+                            uint32_t *e, int64_t *rank, cudaStream_t st);
 cudaError_t launch_rpm(int64_t n, const int32_t *perm, const uint32_t *e, const int64_t *rank,
                        int32_t *rpm_col, cudaStream_t st);
 

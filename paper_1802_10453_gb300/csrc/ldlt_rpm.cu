@@ -21,6 +21,42 @@ namespace {
 
 int64_t g_budget_ns = 2000000000LL;
 
+// ---- profiling (optional) --------------------------------------------------
+struct Prof {
+    bool on = false;
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    cudaEvent_t evs[2][4] = {};  // two sets: panel i uses set i & 1
+    int pending = -1;            // set whose events are recorded but not yet read
+    bool ready = false;
+};
+Prof g_prof;
+
+void prof_init()
+{
+    if (!g_prof.ready) {
+        for (auto &s : g_prof.evs)
+            for (auto &e : s) cudaEventCreate(&e);
+        g_prof.ready = true;
+    }
+}
+
+// Accumulate the phase times of the last recorded panel (its events have
+// completed: the caller synchronised the stream after them).
+void prof_collect()
+{
+    if (g_prof.pending < 0) return;
+    cudaEvent_t *ev = g_prof.evs[g_prof.pending];
+    cudaEventSynchronize(ev[3]);
+    float t01 = 0, t12 = 0, t23 = 0;
+    cudaEventElapsedTime(&t01, ev[0], ev[1]);
+    cudaEventElapsedTime(&t12, ev[1], ev[2]);
+    cudaEventElapsedTime(&t23, ev[2], ev[3]);
+    g_prof.acc[0] += t01;
+    g_prof.acc[1] += t12;
+    g_prof.acc[2] += t23;
+    g_prof.pending = -1;
+}
+
 uint64_t mulmod64(uint64_t a, uint64_t b, uint64_t m) { return (uint64_t)((unsigned __int128)a * b % m); }
 
 uint64_t powmod64(uint64_t a, uint64_t e, uint64_t m)
@@ -70,7 +106,7 @@ int fp64_kred(uint32_t p)
 
 struct Layout {
     int64_t ldS;
-    size_t S0, S1, Lw, LpT, idx0, idx1, sigma, consumed, piv_all, d_all, e_all, zero_all;
+    size_t S0, S1, Lw, LpT, idx0, idx1, sigma, consumed, piv_all, d_all, e_all, zero_all, zero_cols;
     size_t out, sync, events, evvec, scan_min, partner_lp, opA, opB, total;
 };
 
@@ -99,6 +135,7 @@ int make_layout(int64_t n, uint32_t p, int path, Layout &L)
     L.d_all = take((size_t)nn * 4);
     L.e_all = take((size_t)nn * 4);
     L.zero_all = take((size_t)nn * 4);
+    L.zero_cols = take((size_t)nn * 4);
     L.out = take(sizeof(PanelOut));
     L.sync = take(sizeof(PanelSync));
     L.events = take((size_t)MAX_EVENTS * sizeof(Event));
@@ -137,6 +174,26 @@ int check_args(int64_t n, uint32_t p, int path)
 }  // namespace
 
 extern "C" int ldlt_rpm_version(void) { return 10000; }
+
+extern "C" void ldlt_rpm_profile_enable(int on)
+{
+    g_prof.on = on != 0;
+    if (g_prof.on) prof_init();
+}
+
+extern "C" void ldlt_rpm_profile_reset(void)
+{
+    for (double &a : g_prof.acc) a = 0.0;
+    g_prof.pending = -1;
+}
+
+extern "C" int ldlt_rpm_profile_read(double out[8])
+{
+    if (!out) return LDLT_ERR_ARG;
+    prof_collect();
+    for (int i = 0; i < 8; ++i) out[i] = g_prof.acc[i];
+    return LDLT_OK;
+}
 
 extern "C" void ldlt_rpm_set_wait_budget_ns(int64_t ns) { g_budget_ns = ns > 0 ? ns : 2000000000LL; }
 
@@ -189,6 +246,7 @@ extern "C" int ldlt_rpm_factor(int64_t n, uint32_t p, uint32_t *A, int64_t lda, 
     uint32_t *d_all = (uint32_t *)(w + Lo.d_all);
     uint32_t *e_all = (uint32_t *)(w + Lo.e_all);
     int *zero_all = (int *)(w + Lo.zero_all);
+    int *zero_cols = (int *)(w + Lo.zero_cols);
     PanelOut *out = (PanelOut *)(w + Lo.out);
     PanelSync *sync = (PanelSync *)(w + Lo.sync);
     const int64_t ldS = Lo.ldS;
@@ -196,9 +254,12 @@ extern "C" int ldlt_rpm_factor(int64_t n, uint32_t p, uint32_t *A, int64_t lda, 
     const int limbs = (path == LDLT_PATH_TC) ? tc_limbs(p) : 0;
 
     CK(launch_ingest(A, lda, n, Sbuf[0], ldS, idxb[0], f, st));
+    const bool prof = g_prof.on;
+    if (prof) g_prof.acc[5] += 1;
 
-    int m = (int)n, r0 = 0, z0 = 0, cur = 0;
+    int m = (int)n, r0 = 0, z0 = 0, cur = 0, ipanel = 0;
     while (m > 0) {
+        cudaEvent_t *ev = g_prof.evs[ipanel & 1];
         CK(cudaMemset2DAsync(LpT, (size_t)ldS * 4, 0, (size_t)m * 4, KP_MAX, st));
         CK(cudaMemsetAsync(consumed, 0, (size_t)m, st));
         CK(cudaMemsetAsync(sync, 0, sizeof(PanelSync), st));
@@ -217,14 +278,24 @@ extern "C" int ldlt_rpm_factor(int64_t n, uint32_t p, uint32_t *A, int64_t lda, 
             grid = need < nsm ? need : nsm;
             if (grid > MAX_GRID) grid = MAX_GRID;
         }
+        if (prof) CK(cudaEventRecord(ev[0], st));
         CK(launch_panel(pp, grid, st));
-        CK(launch_record_panel(out, idxb[cur], r0, z0, piv_all, d_all, e_all, zero_all, st));
+        CK(launch_record_panel(out, idxb[cur], r0, z0, piv_all, d_all, e_all, zero_all, zero_cols, st));
         int hdr[8];
         CK(cudaMemcpyAsync(hdr, out, sizeof(hdr), cudaMemcpyDeviceToHost, st));
+        if (prof) CK(cudaEventRecord(ev[1], st));
         CK(cudaStreamSynchronize(st));
+        if (prof) prof_collect();  // the previous panel's events precede this sync
         const int np = hdr[0], nzero = hdr[1], m_next = hdr[3], aborted = hdr[4];
+        if (prof) {
+            g_prof.acc[5] += 2;  // panel, record
+            g_prof.acc[6] += 1;
+            g_prof.acc[7] += hdr[5];
+        }
         if (aborted) return LDLT_OK;  // LDLT_ERR_TIMEOUT is in *status
         CK(launch_lw_scatter(LpT, ldS, m, np, idxb[cur], Lw, ldS, r0, st));
+        if (prof && np > 0) g_prof.acc[5] += 1;
+        bool upd = false;
         if (m_next > 0) {
             if (np > 0) {
                 const int kpad = (int)round_up(np, 64);
@@ -232,6 +303,8 @@ extern "C" int ldlt_rpm_factor(int64_t n, uint32_t p, uint32_t *A, int64_t lda, 
                     double *GDT = (double *)(w + Lo.opA);
                     double *GT = GDT + (size_t)KP_MAX * ldS;
                     CK(launch_split_fp64(LpT, ldS, sigma, m_next, np, out, f, GDT, GT, ldS, kpad, st));
+                    if (prof) CK(cudaEventRecord(ev[2], st));
+                    upd = true;
                     CK(launch_syrdk_fp64(Sbuf[cur], ldS, sigma, m_next, GDT, GT, ldS, kpad, f,
                                          Sbuf[cur ^ 1], st));
                 } else {
@@ -239,19 +312,34 @@ extern "C" int ldlt_rpm_factor(int64_t n, uint32_t p, uint32_t *A, int64_t lda, 
                     const size_t aBytes = (size_t)round_up(round_up(n, 128) * (int64_t)limbs * KP_MAX * 2, 256);
                     uint8_t *opB = opA + aBytes;
                     CK(launch_split_tc(LpT, ldS, sigma, m_next, np, out, f, limbs, kpad, opA, opB, st));
+                    if (prof) CK(cudaEventRecord(ev[2], st));
+                    upd = true;
                     CK(launch_syrdk_tc(Sbuf[cur], ldS, sigma, m_next, opA, opB, limbs, kpad, f,
                                        Sbuf[cur ^ 1], g_budget_ns, status, nsm, st));
                 }
             } else {
                 CK(launch_compact_copy(Sbuf[cur], ldS, sigma, m_next, Sbuf[cur ^ 1], st));
+                if (prof) g_prof.acc[5] += 1;
+            }
+        }
+        if (prof) {
+            if (!upd) CK(cudaEventRecord(ev[2], st));
+            CK(cudaEventRecord(ev[3], st));
+            g_prof.pending = ipanel & 1;
+            if (upd) {
+                g_prof.acc[3] += (double)m_next * (double)(m_next + 1) * 0.5 * (double)np;
+                g_prof.acc[4] += 1;
+                g_prof.acc[5] += 2;  // split, update
             }
         }
         r0 += np;
         z0 += nzero;
         cur ^= 1;
         m = m_next;
+        ++ipanel;
     }
-    CK(launch_finalize(n, Lw, ldS, piv_all, d_all, e_all, zero_all, r0, A, lda, perm, e, rank, st));
+    CK(launch_finalize(n, Lw, ldS, piv_all, d_all, e_all, zero_all, zero_cols, r0, A, lda, perm, e, rank, st));
+    if (prof) g_prof.acc[5] += 1;
     return LDLT_OK;
 }
 

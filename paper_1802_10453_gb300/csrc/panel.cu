@@ -191,6 +191,7 @@ struct LeaderShared {
     uint32_t dval[KP_MAX], eval[KP_MAX];
     int piv_rows[KP_MAX];
     int zero_rows[W0];
+    int zero_np[W0];
     uint8_t wstate[W0];
     uint64_t red[32];
     int redi[32];
@@ -329,7 +330,7 @@ __device__ void leader_loop(const PanelParams &P, bool helpers)
             // ---- zero row ----
             __syncthreads();
             if (tid == 0) {
-                sh.zero_rows[sh.nzero] = a; sh.nzero += 1;
+                sh.zero_rows[sh.nzero] = a; sh.zero_np[sh.nzero] = np; sh.nzero += 1;
                 sh.wstate[a] = 1; sh.ia = ia + 1;
             }
             __syncthreads();
@@ -387,7 +388,10 @@ __device__ void leader_loop(const PanelParams &P, bool helpers)
         P.out->dval[k] = sh.dval[k];
         P.out->eval[k] = sh.eval[k];
     }
-    for (int q = tid; q < nzero; q += blockDim.x) P.out->zero_rows[q] = sh.zero_rows[q];
+    for (int q = tid; q < nzero; q += blockDim.x) {
+        P.out->zero_rows[q] = sh.zero_rows[q];
+        P.out->zero_np[q] = sh.zero_np[q];
+    }
 
     // ---- compaction of the remaining rows [iend, m) minus consumed partners ----
     const int m = P.m;
