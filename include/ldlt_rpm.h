@@ -134,12 +134,15 @@ void ldlt_rpm_set_wait_budget_ns(int64_t ns);
  *   out[5] number of kernels this library launched
  *   out[6] number of panels
  *   out[7] far scans issued by the pivot chain
+ *   out[8..15] SM clock cycles the pivot chain's leader spent per phase:
+ *          candidate column, wait for pivot inverse, 1x1 store, search,
+ *          scan request, scan wait, zero row, 2x2 pivot
  * ldlt_rpm_profile_read returns LDLT_OK, or LDLT_ERR_ARG for a NULL pointer.
  * The counters are process-wide and not thread-safe.
  */
 void ldlt_rpm_profile_enable(int on);
 void ldlt_rpm_profile_reset(void);
-int ldlt_rpm_profile_read(double out[8]);
+int ldlt_rpm_profile_read(double out[16]);
 
 #ifdef __cplusplus
 }

@@ -10,8 +10,10 @@
 // window of the first W0 remaining rows; its far rows are shared by helper CTAs.
 constexpr int KP_MAX = 128;
 constexpr int W0 = 256;
-constexpr int PANEL_THREADS = 256;   // one thread per window row
+constexpr int ROWS_PER_HELPER = 256;  // far rows per helper CTA kept in shared memory
+constexpr int PANEL_THREADS_V2 = 576; // 16 compute warps (two threads per row) + 2 service warps
 constexpr int MAX_EVENTS = 2 * W0 + 4;
+constexpr int EV_WORDS = 4 * KP_MAX;  // payload words per event
 
 // Row storage of the Schur complement and of L: leading dimension rounded up so
 // every row starts on a 256-byte boundary.
@@ -23,9 +25,9 @@ enum EventKind : int { EV_PIVOT1 = 1, EV_PIVOT2 = 2, EV_SCAN = 3, EV_END = 4 };
 struct Event {
     int kind;
     int a, b;        // compact rows of the pivot (b only for 2x2)
-    int np;          // pivots before this event (length of the v vectors)
-    uint32_t s0;     // 1x1: d^{-1}; 2x2: x^{-1}
-    uint32_t s1;     // 2x2: delta (y/2 for odd p, y for p = 2)
+    int np;          // pivots before this event (length of the z vectors)
+    uint32_t s0;     // the scale W of the division-free Crout form
+    uint32_t s1;
     int scan_id;     // EV_SCAN: sequence number of the scan
     int pad;
 };
@@ -47,6 +49,7 @@ struct PanelOut {
     int abort;
     int nscan;       // far scans issued (diagnostics)
     int pad[2];
+    long long cyc[8];       // leader clock64 cycles per phase (diagnostics)
     int piv_rows[KP_MAX];   // compact rows, pivot order
     uint32_t dval[KP_MAX];  // D diagonal
     uint32_t eval[KP_MAX];  // x at a 2x2 block start, else 0
@@ -70,8 +73,8 @@ struct PanelParams {
     PanelOut *out;
     PanelSync *sync;
     Event *events;
-    uint32_t *evvec;        // [MAX_EVENTS][2][KP_MAX]
-    int *scan_min;          // [gridDim.x]
+    uint32_t *evvec;        // [MAX_EVENTS][EV_WORDS]
+    int *scan_min;          // [MAX_EVENTS]: first non-zero row of each far scan (atomicMin)
     uint32_t *partner_lp;   // [gridDim.x][KP_MAX]
     int64_t budget_ns;
     int32_t *status;

@@ -11,6 +11,7 @@
 //                        (SYRDK, FP64 or tensor-core form), rows compacted
 //   finalize: A <- L in perm order with D on the diagonal (PERM)
 // After each panel three words are read back to size the next launches.
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 
@@ -24,7 +25,7 @@ int64_t g_budget_ns = 2000000000LL;
 // ---- profiling (optional) --------------------------------------------------
 struct Prof {
     bool on = false;
-    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double acc[16] = {};
     cudaEvent_t evs[2][4] = {};  // two sets: panel i uses set i & 1
     int pending = -1;            // set whose events are recorded but not yet read
     bool ready = false;
@@ -139,8 +140,8 @@ int make_layout(int64_t n, uint32_t p, int path, Layout &L)
     L.out = take(sizeof(PanelOut));
     L.sync = take(sizeof(PanelSync));
     L.events = take((size_t)MAX_EVENTS * sizeof(Event));
-    L.evvec = take((size_t)MAX_EVENTS * 2 * KP_MAX * 4);
-    L.scan_min = take((size_t)MAX_GRID * 4);
+    L.evvec = take((size_t)MAX_EVENTS * EV_WORDS * 4);
+    L.scan_min = take((size_t)MAX_EVENTS * 4);
     L.partner_lp = take((size_t)MAX_GRID * KP_MAX * 4);
     if (path == LDLT_PATH_FP64) {
         L.opA = take(fp64_operand_bytes(nn));
@@ -187,11 +188,11 @@ extern "C" void ldlt_rpm_profile_reset(void)
     g_prof.pending = -1;
 }
 
-extern "C" int ldlt_rpm_profile_read(double out[8])
+extern "C" int ldlt_rpm_profile_read(double out[16])
 {
     if (!out) return LDLT_ERR_ARG;
     prof_collect();
-    for (int i = 0; i < 8; ++i) out[i] = g_prof.acc[i];
+    for (int i = 0; i < 16; ++i) out[i] = g_prof.acc[i];
     return LDLT_OK;
 }
 
@@ -263,6 +264,7 @@ extern "C" int ldlt_rpm_factor(int64_t n, uint32_t p, uint32_t *A, int64_t lda, 
         CK(cudaMemset2DAsync(LpT, (size_t)ldS * 4, 0, (size_t)m * 4, KP_MAX, st));
         CK(cudaMemsetAsync(consumed, 0, (size_t)m, st));
         CK(cudaMemsetAsync(sync, 0, sizeof(PanelSync), st));
+        CK(cudaMemsetAsync(w + Lo.scan_min, 0x7F, (size_t)MAX_EVENTS * 4, st));  // "no hit" > any row
         PanelParams pp;
         pp.S = Sbuf[cur]; pp.ldS = ldS; pp.m = m; pp.f = f;
         pp.kp = KP_MAX; pp.w = m < W0 ? m : W0;
@@ -274,15 +276,17 @@ extern "C" int ldlt_rpm_factor(int64_t n, uint32_t p, uint32_t *A, int64_t lda, 
         pp.budget_ns = g_budget_ns; pp.status = status;
         int grid = 1;
         if (m > pp.w) {
-            const int need = 1 + (m - pp.w + PANEL_THREADS - 1) / PANEL_THREADS;
+            const int need = 1 + (m - pp.w + ROWS_PER_HELPER - 1) / ROWS_PER_HELPER;
             grid = need < nsm ? need : nsm;
             if (grid > MAX_GRID) grid = MAX_GRID;
         }
         if (prof) CK(cudaEventRecord(ev[0], st));
         CK(launch_panel(pp, grid, st));
         CK(launch_record_panel(out, idxb[cur], r0, z0, piv_all, d_all, e_all, zero_all, zero_cols, st));
-        int hdr[8];
-        CK(cudaMemcpyAsync(hdr, out, sizeof(hdr), cudaMemcpyDeviceToHost, st));
+        struct { int h[8]; long long cyc[8]; } rb;
+        static_assert(offsetof(PanelOut, cyc) == 8 * sizeof(int), "PanelOut layout");
+        CK(cudaMemcpyAsync(&rb, out, sizeof(rb), cudaMemcpyDeviceToHost, st));
+        const int *hdr = rb.h;
         if (prof) CK(cudaEventRecord(ev[1], st));
         CK(cudaStreamSynchronize(st));
         if (prof) prof_collect();  // the previous panel's events precede this sync
@@ -291,6 +295,7 @@ extern "C" int ldlt_rpm_factor(int64_t n, uint32_t p, uint32_t *A, int64_t lda, 
             g_prof.acc[5] += 2;  // panel, record
             g_prof.acc[6] += 1;
             g_prof.acc[7] += hdr[5];
+            for (int i = 0; i < 8; ++i) g_prof.acc[8 + i] += (double)rb.cyc[i];
         }
         if (aborted) return LDLT_OK;  // LDLT_ERR_TIMEOUT is in *status
         CK(launch_lw_scatter(LpT, ldS, m, np, idxb[cur], Lw, ldS, r0, st));

@@ -5,23 +5,46 @@
 //   * a 1x1 pivot if its diagonal entry c_a[a] is non-zero;
 //   * a 2x2 pivot with b, the first index > a with c_a[b] != 0;
 //   * a non-pivot row if its Schur row is zero.
-// c_a[t] = S[t][a] - sum_k Lp[t][k] (D Lp[a])_k is the Crout form of the Schur
+// c_a[t] = S[t][a] - sum_k L[t][k] (D L[a])_k is the Crout form of the Schur
 // entry (the "c <- A_{i..n,i} - N v^T" step of Algorithm 4, with D in place of
-// the printed D^{-1}); Lp holds the L columns of the pivots taken so far in
-// this panel.  After a 1x1 pivot the new column is c_a / d; after a 2x2 pivot
-// the columns of a and b are alpha_t = (c_b[t] - delta beta_t)/x and
-// beta_t = c_a[t]/x (Algorithm 4, 2x2 branch: delta = y/2 for odd p, y for p = 2).
+// the printed D^{-1}).
+//
+// Division-free form.  A modular inverse is a long serial computation; taking
+// one per pivot on the decision path would dominate the chain.  The panel
+// therefore keeps, for every row t, the unscaled Schur columns U~[t][k] and,
+// per pivot block B, an integer 2x2 (or 1x1) form M_B and a non-zero
+// "denominator" delta_B such that the block's share of the Crout sum is
+//   U~[t][B] M_B U~[a][B]^T / delta_B.
+// With W = prod_B delta_B and w_B = W / delta_B (both kept by multiplication
+// only) the scaled Schur entry is
+//   c~_a[t] = W c_a[t] = W S[t][a] - sum_k U~[t][k] z_a[k],
+//   z_a = concat_B  M_B U~[a][B]^T w_B,
+// and c~ is zero exactly when c is.  A 1x1 pivot stores U~[:, j] = c~_a
+// (M = 1, delta = W c~_a[a]); a 2x2 pivot stores c~_a and c~_b
+// (M = [[-y~, x~], [x~, 0]], delta = W x~^2, x~ = c~_a[b], y~ = c~_b[b]).  The
+// block forms follow from Algorithm 4's 2x2 branch: with beta = c_a / x,
+// alpha = (c_b - delta' beta) / x and D = [[0,x],[x,y']], the product
+// [alpha, beta] D [alpha', beta']^T equals [c_a, c_b] [[-y/x^2, 1/x],[1/x, 0]]
+// [c_a', c_b']^T for both odd p (y' = 0, delta' = y/2) and p = 2 (y' = delta'
+// = y).  At the end of the panel all inverses are taken at once (Montgomery's
+// batch inversion) and every CTA rewrites its U~ rows as the true L columns;
+// D is reported in true values.  The results are identical to the divided
+// form because all arithmetic is exact.
 //
 // GPU organisation.  One cooperative launch per panel.  CTA 0 (the leader)
 // owns the window of the first W rows of S and takes every decision.  The
-// other CTAs (helpers) own the far rows [W, m) in contiguous slices; they
-// compute the new L columns of their rows as the leader publishes pivots
-// (an ordered event queue in global memory), and answer "far scans": when a
-// row has no non-zero inside the window, every helper searches its slice for
-// the first non-zero of that row and the leader takes the minimum.  Helpers
-// never block the leader except during a far scan.  Every wait is bounded by
-// a %globaltimer budget; when it runs out the kernel writes LDLT_ERR_TIMEOUT
-// to the status word, raises an abort flag the other CTAs poll, and returns.
+// other CTAs (helpers) own the far rows [W, m) in contiguous slices.  Each CTA
+// keeps the U~ columns of its rows in shared memory (k-major, padded) and
+// writes them through to global memory.  16 compute warps work two threads
+// per row.  In the leader, warp 17 publishes events to the helpers from a
+// shared-memory ring so the gpu-scope fence stays off the critical path; in a
+// helper, warp 16 prefetches events into the ring.  Helpers compute the new
+// columns of their rows as pivots are published and answer "far scans": when
+// a row has no non-zero inside the window, every helper searches its slice
+// for the first non-zero of that row and the leader takes the minimum.  Every
+// wait is bounded by a %globaltimer budget; when it runs out the kernel
+// writes LDLT_ERR_TIMEOUT to the status word, raises an abort flag the other
+// CTAs poll, and returns.
 //
 // At the end the leader compacts the remaining rows (order preserved) into
 // sigma / idx_next for the next Schur complement.
@@ -33,6 +56,18 @@
 
 namespace {
 
+constexpr int NCW = 16;                       // compute warps
+constexpr int NCT = NCW * 32;                 // compute threads (2 per row)
+constexpr int SROWS = 256;                    // rows held in shared memory per CTA
+constexpr int SSTRIDE = SROWS + 16;           // padded k-row stride (words)
+constexpr int NSLOT = 8;                      // event ring slots
+constexpr int BLOCK = PANEL_THREADS_V2;
+
+static_assert(BLOCK == NCT + 64, "two service warps");
+static_assert(W0 <= SROWS && ROWS_PER_HELPER <= SROWS, "rows fit in shared memory");
+
+enum ColKind : uint8_t { K_1x1 = 1, K_2A = 2, K_2B = 3 };
+
 __device__ __forceinline__ int64_t gtime()
 {
     uint64_t t;
@@ -40,67 +75,48 @@ __device__ __forceinline__ int64_t gtime()
     return (int64_t)t;
 }
 
+// barrier among the 16 compute warps only
+__device__ __forceinline__ void cbar() { asm volatile("bar.sync 1, %0;" ::"n"(NCT) : "memory"); }
+
 __device__ __forceinline__ uint32_t s_at(const uint32_t *__restrict__ S, int64_t ldS, int i, int j)
 {
     return i >= j ? __ldg(S + (int64_t)i * ldS + j) : __ldg(S + (int64_t)j * ldS + i);
 }
 
-// sum over the CTA of values < 2^32 (at most 2^10 of them)
-__device__ uint64_t block_sum(uint64_t v, uint64_t *red)
+template <bool BIG>
+__device__ __forceinline__ void mac(uint64_t &acc, uint32_t a, uint32_t b, const FieldP &f)
 {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    __syncthreads();
-    if (l == 0) red[w] = v;
-    __syncthreads();
-    uint64_t s = 0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
-    return s;
+    acc += (uint64_t)a * (uint64_t)b;
+    if (BIG) acc -= (acc >> 63) * f.m63;
 }
 
-__device__ int block_min(int v, int *redi)
-{
-    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
-    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    __syncthreads();
-    if (l == 0) redi[w] = v;
-    __syncthreads();
-    int s = INT_MAX;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s = min(s, redi[i]);
-    return s;
-}
-
-// (D l)_k for the block diagonal D of this panel (eval[k] != 0 marks the start
-// of a 2x2 block [[0,x],[x,dval[k+1]]]).
-__device__ __forceinline__ uint32_t dmul(int k, const uint32_t *l, const uint32_t *dval,
-                                         const uint32_t *eval, const FieldP &f)
-{
-    if (eval[k] != 0) return fp_mul(eval[k], l[k + 1], f);
-    if (k > 0 && eval[k - 1] != 0)
-        return fp_add(fp_mul(eval[k - 1], l[k - 1], f), fp_mul(dval[k], l[k], f), f);
-    return fp_mul(dval[k], l[k], f);
-}
-
-// c_v[t] = S(t, a) - sum_{k < np} Lp[t][k] v[k]
-__device__ __forceinline__ uint32_t schur_entry(const PanelParams &P, int t, int a,
-                                                const uint32_t *v, int np)
-{
-    uint64_t acc = 0;
-    const uint32_t *col = P.LpT + t;
-    int k = 0;
-    for (; k + 4 <= np; k += 4) {
-        uint32_t l0 = col[(int64_t)(k + 0) * P.ldL];
-        uint32_t l1 = col[(int64_t)(k + 1) * P.ldL];
-        uint32_t l2 = col[(int64_t)(k + 2) * P.ldL];
-        uint32_t l3 = col[(int64_t)(k + 3) * P.ldL];
-        fp_mac(acc, l0, v[k + 0], P.f);
-        fp_mac(acc, l1, v[k + 1], P.f);
-        fp_mac(acc, l2, v[k + 2], P.f);
-        fp_mac(acc, l3, v[k + 3], P.f);
-    }
-    for (; k < np; ++k) fp_mac(acc, col[(int64_t)k * P.ldL], v[k], P.f);
-    return fp_sub(s_at(P.S, P.ldS, t, a), fp_reduce64(acc, P.f), P.f);
-}
+struct Shared {
+    uint32_t U[KP_MAX * SSTRIDE];      // U~ columns of this CTA's rows, k-major
+    uint32_t ring[NSLOT][EV_WORDS];    // event payloads
+    Event ev[NSLOT];
+    uint32_t za[KP_MAX], zb[KP_MAX], ub[KP_MAX];
+    uint8_t kind[KP_MAX];              // column kinds of this panel
+    uint32_t bw[KP_MAX];               // w_B, at the block's first column
+    uint32_t mx[KP_MAX], my[KP_MAX];   // x~, y~ of a 2x2 block (first column)
+    uint32_t piv[KP_MAX];              // c~_a[a] (1x1) or x~ (2x2) at the first column
+    uint32_t w0[KP_MAX];               // W when the block was formed
+    uint32_t cA[KP_MAX], cB[KP_MAX];   // true-L coefficients (end of panel)
+    uint32_t dtrue[KP_MAX], etrue[KP_MAX];
+    uint32_t bi[2 * KP_MAX];           // batch inversion: values, then their inverses
+    uint32_t bpre[2 * KP_MAX];         // batch inversion: prefix products
+    int piv_rows[KP_MAX];
+    int zero_rows[W0];
+    int zero_np[W0];
+    uint8_t wstate[W0];
+    int redi[32];
+    uint32_t xy[4];
+    uint32_t caa;
+    volatile int ev_ready;             // events written to the ring (leader) / fetched (helper)
+    volatile int ev_done;              // events published (leader) / processed (helper)
+    volatile int quit;
+    uint32_t W;
+    int np, ia, nzero, nscan, abort, b, owner, nblk;
+};
 
 __device__ void raise_timeout(const PanelParams &P)
 {
@@ -108,193 +124,347 @@ __device__ void raise_timeout(const PanelParams &P)
     atomicExch(&P.sync->abort, 1);
 }
 
+// z[k] of row u (u read with a stride): M_B U~[u][B]^T w_B per block.
+__device__ __forceinline__ uint32_t zval(int k, const uint32_t *u, int stride, const Shared &sh, const FieldP &f)
+{
+    const uint8_t kd = sh.kind[k];
+    if (kd == K_1x1) return fp_mul(u[k * stride], sh.bw[k], f);
+    if (kd == K_2A)
+        return fp_mul(fp_sub(fp_mul(sh.mx[k], u[(k + 1) * stride], f), fp_mul(sh.my[k], u[k * stride], f), f),
+                      sh.bw[k], f);
+    return fp_mul(fp_mul(sh.mx[k - 1], u[(k - 1) * stride], f), sh.bw[k - 1], f);
+}
+
+// c~_z[t] = W S(t, a) - sum_{k < np} U~[t][k] z[k], two threads per row (half
+// = tid & 1 takes every other k).  All 32 lanes must call it (pair shuffle);
+// invalid rows compute nothing and return 0.
+template <bool BIG>
+__device__ __forceinline__ uint32_t schur2(const PanelParams &P, const uint32_t *sU, int lrow, int grow, int a,
+                                          uint32_t W, const uint32_t *z, int np, int half, bool valid,
+                                          bool in_smem)
+{
+    uint64_t acc = 0;
+    if (valid) {
+        if (in_smem) {
+            const uint32_t *col = sU + lrow;
+#pragma unroll 4
+            for (int k = half; k < np; k += 2) mac<BIG>(acc, col[k * SSTRIDE], z[k], P.f);
+        } else {
+            const uint32_t *col = P.LpT + grow;
+            for (int k = half; k < np; k += 2) mac<BIG>(acc, col[(int64_t)k * P.ldL], z[k], P.f);
+        }
+    }
+    const uint32_t part = fp_reduce64(acc, P.f);
+    const uint32_t other = __shfl_xor_sync(0xffffffffu, part, 1);
+    if (!valid) return 0u;
+    return fp_sub(fp_mul(W, s_at(P.S, P.ldS, grow, a), P.f), fp_add(part, other, P.f), P.f);
+}
+
+// Rewrite the U~ values of one row as true L values (in global memory), using
+// the per-column coefficients: 1x1: L_j = cA_j U_j; first column of a 2x2:
+// L_j = cA_j U_{j+1} + cB_j U_j; second column: L_j = cA_j U_{j-1}.
+__device__ __forceinline__ void finish_row(const PanelParams &P, const uint32_t *u, int stride, uint32_t *g,
+                                           int np, const uint8_t *kind, const uint32_t *cA, const uint32_t *cB)
+{
+    for (int j = 0; j < np; ++j) {
+        const uint8_t kd = kind[j];
+        if (kd == K_1x1) {
+            g[(int64_t)j * P.ldL] = fp_mul(cA[j], u[j * stride], P.f);
+        } else if (kd == K_2A) {
+            const uint32_t u0 = u[j * stride], u1 = u[(j + 1) * stride];
+            g[(int64_t)j * P.ldL] = fp_add(fp_mul(cA[j], u1, P.f), fp_mul(cB[j], u0, P.f), P.f);
+            g[(int64_t)(j + 1) * P.ldL] = fp_mul(cA[j + 1], u0, P.f);
+            ++j;
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // helper CTAs
 // ---------------------------------------------------------------------------
-__device__ void helper_loop(const PanelParams &P, int lo, int hi)
+template <bool BIG>
+__device__ void helper_cta(const PanelParams &P, Shared &sh, int lo, int hi)
 {
-    __shared__ uint32_t sv_a[KP_MAX], sv_b[KP_MAX];
-    __shared__ Event ev;
-    __shared__ int s_go;
-    __shared__ int redi[32];
     const int tid = threadIdx.x;
-    const int cta = blockIdx.x;
-    for (int e = 0;; ++e) {
-        if (tid == 0) {
+    const int warp = tid >> 5, lane = tid & 31;
+    const int nrows = hi > lo ? hi - lo : 0;
+    if (tid == 0) { sh.ev_ready = 0; sh.ev_done = 0; sh.quit = 0; }
+    __syncthreads();
+
+    if (warp == NCW) {
+        // ---- poller: fetch events into the shared ring ----
+        for (int e = 0;; ++e) {
             int go = 0;
-            int64_t t0 = gtime();
-            volatile int *cnt = &P.sync->ev_count;
-            volatile int *ab = &P.sync->abort;
-            for (;;) {
-                if (*cnt > e) { go = 1; break; }
-                if (*ab) break;
-                if (gtime() - t0 > P.budget_ns) { raise_timeout(P); break; }
+            if (lane == 0) {
+                const int64_t t0 = gtime();
+                volatile int *cnt = &P.sync->ev_count;
+                volatile int *ab = &P.sync->abort;
+                for (;;) {
+                    if (*cnt > e && sh.ev_done > e - NSLOT) { go = 1; break; }
+                    if (*ab) break;
+                    if (gtime() - t0 > P.budget_ns) { raise_timeout(P); break; }
+                }
+            }
+            go = __shfl_sync(0xffffffffu, go, 0);
+            if (!go) {
+                if (lane == 0) { __threadfence_block(); sh.quit = 1; }
+                return;
             }
             __threadfence();
-            if (go) {
-                ev.kind = __ldcg(&P.events[e].kind);
-                ev.a = __ldcg(&P.events[e].a);
-                ev.b = __ldcg(&P.events[e].b);
-                ev.np = __ldcg(&P.events[e].np);
-                ev.s0 = __ldcg(&P.events[e].s0);
-                ev.s1 = __ldcg(&P.events[e].s1);
-                ev.scan_id = __ldcg(&P.events[e].scan_id);
+            const int s = e % NSLOT;
+            const int *gh = reinterpret_cast<const int *>(&P.events[e]);
+            const int hv = lane < 8 ? __ldcg(gh + lane) : 0;
+            const int kind = __shfl_sync(0xffffffffu, hv, 0);
+            const int np = __shfl_sync(0xffffffffu, hv, 3);
+            if (lane < 8) reinterpret_cast<int *>(&sh.ev[s])[lane] = hv;
+            const uint32_t *vv = P.evvec + (int64_t)e * EV_WORDS;
+            const int words = (kind == EV_END) ? 3 * KP_MAX : (kind == EV_PIVOT2 ? 2 * KP_MAX : KP_MAX);
+            for (int k = lane; k < words; k += 32) {
+                const int part = k / KP_MAX, kk = k % KP_MAX;
+                if (kind == EV_END || kk < np) sh.ring[s][k] = __ldcg(vv + (int64_t)part * KP_MAX + kk);
             }
-            s_go = go;
+            __threadfence_block();
+            __syncwarp();
+            if (lane == 0) sh.ev_ready = e + 1;
+            if (kind == EV_END) return;
         }
-        __syncthreads();
-        if (!s_go || ev.kind == EV_END) return;
-        const int np = ev.np, a = ev.a, b = ev.b, kind = ev.kind;
-        const uint32_t *vv = P.evvec + (int64_t)e * 2 * KP_MAX;
-        for (int k = tid; k < np; k += blockDim.x) {
-            sv_a[k] = __ldcg(vv + k);
-            if (kind == EV_PIVOT2) sv_b[k] = __ldcg(vv + KP_MAX + k);
+    }
+    if (warp > NCW) return;  // the second service warp has no work in a helper
+
+    // ---- compute warps ----
+    const int half = tid & 1;
+    for (int e = 0;; ++e) {
+        if (tid == 0) {
+            const int64_t t0 = gtime();
+            while (sh.ev_ready <= e && !sh.quit) {
+                if (gtime() - t0 > 2 * P.budget_ns + 1000000) break;
+            }
         }
-        __syncthreads();
+        cbar();
+        if (sh.ev_ready <= e) return;  // quit or abort
+        __threadfence_block();
+        const int s = e % NSLOT;
+        const int kind = sh.ev[s].kind;
+        const int np = sh.ev[s].np, a = sh.ev[s].a, b = sh.ev[s].b;
+        const uint32_t W = sh.ev[s].s0;
+        const uint32_t *za = sh.ring[s];
+        const uint32_t *zb = sh.ring[s] + KP_MAX;
+        if (kind == EV_END) {
+            // rewrite this CTA's rows as true L columns
+            const uint32_t *kinds = sh.ring[s];
+            const uint32_t *cA = sh.ring[s] + KP_MAX;
+            const uint32_t *cB = sh.ring[s] + 2 * KP_MAX;
+            __shared__ uint8_t kb[KP_MAX];
+            for (int k = tid; k < np; k += NCT) kb[k] = (uint8_t)kinds[k];
+            cbar();
+            for (int lr = tid; lr < nrows; lr += NCT) {
+                const int t = lo + lr;
+                if (lr < SROWS) finish_row(P, sh.U + lr, SSTRIDE, P.LpT + t, np, kb, cA, cB);
+                else finish_row(P, P.LpT + t, (int)P.ldL, P.LpT + t, np, kb, cA, cB);
+            }
+            return;
+        }
         int firstnz = INT_MAX;
-        for (int t = lo + tid; t < hi; t += blockDim.x) {
+        for (int base = 0; base < nrows; base += NCT / 2) {
+            const int lr = base + (tid >> 1);
+            const bool valid = lr < nrows;
+            const bool sm = lr < SROWS;
+            const int t = lo + lr;
             if (kind == EV_PIVOT1) {
-                uint32_t c = schur_entry(P, t, a, sv_a, np);
-                P.LpT[(int64_t)np * P.ldL + t] = fp_mul(c, ev.s0, P.f);
+                const uint32_t c = schur2<BIG>(P, sh.U, lr, t, a, W, za, np, half, valid, sm);
+                if (valid && half == 0) {
+                    if (sm) sh.U[np * SSTRIDE + lr] = c;
+                    P.LpT[(int64_t)np * P.ldL + t] = c;
+                }
             } else if (kind == EV_PIVOT2) {
-                uint32_t ca = schur_entry(P, t, a, sv_a, np);
-                uint32_t cb = schur_entry(P, t, b, sv_b, np);
-                uint32_t beta = fp_mul(ca, ev.s0, P.f);
-                uint32_t alpha = fp_mul(fp_sub(cb, fp_mul(beta, ev.s1, P.f), P.f), ev.s0, P.f);
-                P.LpT[(int64_t)np * P.ldL + t] = alpha;
-                P.LpT[(int64_t)(np + 1) * P.ldL + t] = beta;
+                const uint32_t ca = schur2<BIG>(P, sh.U, lr, t, a, W, za, np, half, valid, sm);
+                const uint32_t cb = schur2<BIG>(P, sh.U, lr, t, b, W, zb, np, half, valid, sm);
+                if (valid && half == 0) {
+                    if (sm) { sh.U[np * SSTRIDE + lr] = ca; sh.U[(np + 1) * SSTRIDE + lr] = cb; }
+                    P.LpT[(int64_t)np * P.ldL + t] = ca;
+                    P.LpT[(int64_t)(np + 1) * P.ldL + t] = cb;
+                }
             } else {  // EV_SCAN
-                uint32_t c = schur_entry(P, t, a, sv_a, np);
-                if (c != 0 && t < firstnz) firstnz = t;
+                const uint32_t c = schur2<BIG>(P, sh.U, lr, t, a, W, za, np, half, valid, sm);
+                if (valid && c != 0 && t < firstnz) firstnz = t;
             }
         }
         if (kind == EV_SCAN) {
-            int mn = block_min(firstnz, redi);
+            for (int o = 16; o > 0; o >>= 1) firstnz = min(firstnz, __shfl_xor_sync(0xffffffffu, firstnz, o));
+            if (lane == 0) sh.redi[warp] = firstnz;
+            cbar();
+            int mn = INT_MAX;
+            for (int i = 0; i < NCW; ++i) mn = min(mn, sh.redi[i]);
             if (mn != INT_MAX) {
-                for (int k = tid; k < np; k += blockDim.x)
-                    P.partner_lp[(int64_t)cta * KP_MAX + k] = P.LpT[(int64_t)k * P.ldL + mn];
+                const int lr = mn - lo;
+                for (int k = tid; k < np; k += NCT)
+                    P.partner_lp[(int64_t)blockIdx.x * KP_MAX + k] =
+                        lr < SROWS ? sh.U[k * SSTRIDE + lr] : P.LpT[(int64_t)k * P.ldL + mn];
             }
-            if (tid == 0) P.scan_min[cta] = mn;
             __threadfence();
-            __syncthreads();
-            if (tid == 0) atomicAdd(&P.sync->scan_done, 1);
+            cbar();
+            if (tid == 0) {
+                if (mn != INT_MAX) atomicMin(&P.scan_min[sh.ev[s].scan_id], mn);
+                __threadfence();
+                atomicAdd(&P.sync->scan_done, 1);
+            }
         }
-        __syncthreads();
+        cbar();
+        if (tid == 0) { __threadfence_block(); sh.ev_done = e + 1; }
     }
 }
 
 // ---------------------------------------------------------------------------
 // leader CTA
 // ---------------------------------------------------------------------------
-struct LeaderShared {
-    uint32_t va[KP_MAX], vb[KP_MAX], la[KP_MAX], lb[KP_MAX];
-    uint32_t dval[KP_MAX], eval[KP_MAX];
-    int piv_rows[KP_MAX];
-    int zero_rows[W0];
-    int zero_np[W0];
-    uint8_t wstate[W0];
-    uint64_t red[32];
-    int redi[32];
-    int np, ia, nzero, nev, nscan, b, abort;
-    uint32_t x, y;
-};
-
-__device__ void publish(const PanelParams &P, LeaderShared &sh, int kind, int a, int b, int np,
-                        uint32_t s0, uint32_t s1, int scan_id)
+template <bool BIG>
+__device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
 {
     const int tid = threadIdx.x;
-    const int e = sh.nev;
-    uint32_t *vv = P.evvec + (int64_t)e * 2 * KP_MAX;
-    for (int k = tid; k < np; k += blockDim.x) {
-        vv[k] = sh.va[k];
-        if (kind == EV_PIVOT2) vv[KP_MAX + k] = sh.vb[k];
-    }
-    if (tid == 0) {
-        Event *ev = &P.events[e];
-        ev->kind = kind; ev->a = a; ev->b = b; ev->np = np;
-        ev->s0 = s0; ev->s1 = s1; ev->scan_id = scan_id; ev->pad = 0;
-    }
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) {
-        atomicExch(&P.sync->ev_count, e + 1);
-        sh.nev = e + 1;
-    }
-    __syncthreads();
-}
-
-__device__ void leader_loop(const PanelParams &P, bool helpers)
-{
-    __shared__ LeaderShared sh;
-    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
     const FieldP f = P.f;
     const int w = P.w;
     for (int t = tid; t < W0; t += blockDim.x) sh.wstate[t] = 0;
     if (tid == 0) {
-        sh.np = 0; sh.ia = 0; sh.nzero = 0; sh.nev = 0; sh.nscan = 0; sh.abort = 0;
+        sh.np = 0; sh.ia = 0; sh.nzero = 0; sh.nscan = 0; sh.abort = 0; sh.nblk = 0;
+        sh.ev_ready = 0; sh.ev_done = 0; sh.quit = 0; sh.W = 1u;
     }
     __syncthreads();
+
+    if (warp == NCW + 1) {
+        // ---- publisher: ring slot -> global event, fence, then the counter ----
+        if (!helpers) return;
+        for (int e = 0;; ++e) {
+            int ready = 0;
+            if (lane == 0) {
+                const int64_t t0 = gtime();
+                for (;;) {
+                    if (sh.ev_ready > e) { ready = 1; break; }
+                    if (sh.quit) break;
+                    if (gtime() - t0 > 4 * P.budget_ns + 1000000) break;
+                }
+            }
+            ready = __shfl_sync(0xffffffffu, ready, 0);
+            if (!ready) return;
+            __threadfence_block();
+            const int s = e % NSLOT;
+            const int kind = sh.ev[s].kind, np = sh.ev[s].np;
+            uint32_t *vv = P.evvec + (int64_t)e * EV_WORDS;
+            const int words = (kind == EV_END) ? 3 * KP_MAX : (kind == EV_PIVOT2 ? 2 * KP_MAX : KP_MAX);
+            for (int k = lane; k < words; k += 32) {
+                const int kk = k % KP_MAX;
+                if (kind == EV_END || kk < np) vv[k] = sh.ring[s][k];
+            }
+            if (lane < 8) reinterpret_cast<int *>(&P.events[e])[lane] = reinterpret_cast<const int *>(&sh.ev[s])[lane];
+            __threadfence();
+            __syncwarp();
+            if (lane == 0) {
+                atomicExch(&P.sync->ev_count, e + 1);
+                sh.ev_done = e + 1;
+            }
+            __syncwarp();
+            if (kind == EV_END) return;
+        }
+    }
+    if (warp == NCW) return;  // spare service warp
+
+    // ---- compute warps: 512 threads, two per window row ----
+    const int half = tid & 1;
+    const int lr = tid >> 1;  // window row of this thread pair
+    const bool inwin = lr < w;
+
+    // put an event in the ring: payload words are copied from `src` parts
+    auto push_event = [&](int kind, int a, int b, int np, uint32_t s0, int scan_id, const uint32_t *p0,
+                          const uint32_t *p1, const uint32_t *p2, int nwords) {
+        const int e = sh.ev_ready;
+        if (tid == 0) {
+            const int64_t t0 = gtime();
+            while (sh.ev_done <= e - NSLOT) {
+                if (gtime() - t0 > P.budget_ns) { raise_timeout(P); sh.abort = 1; break; }
+            }
+        }
+        cbar();
+        const int s = e % NSLOT;
+        for (int k = tid; k < nwords; k += NCT) {
+            sh.ring[s][k] = p0[k];
+            if (p1) sh.ring[s][KP_MAX + k] = p1[k];
+            if (p2) sh.ring[s][2 * KP_MAX + k] = p2[k];
+        }
+        if (tid == 0) {
+            sh.ev[s].kind = kind; sh.ev[s].a = a; sh.ev[s].b = b; sh.ev[s].np = np;
+            sh.ev[s].s0 = s0; sh.ev[s].s1 = 0; sh.ev[s].scan_id = scan_id; sh.ev[s].pad = 0;
+        }
+        cbar();
+        if (tid == 0) { __threadfence_block(); sh.ev_ready = e + 1; }
+    };
+
+    long long cyc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    long long tmark = clock64();
+    auto lap = [&](int ph) {
+        if (tid == 0) { const long long t = clock64(); cyc[ph] += t - tmark; tmark = t; }
+    };
 
     for (;;) {
         const int np = sh.np, ia = sh.ia;
         if (np > P.kp - 2 || ia >= w || sh.abort) break;
         if (sh.wstate[ia]) {
-            __syncthreads();
+            cbar();
             if (tid == 0) sh.ia = ia + 1;
-            __syncthreads();
+            cbar();
             continue;
         }
         const int a = ia;
-        // L row of a over this panel's columns, then v_a = D l_a
-        for (int k = tid; k < np; k += blockDim.x) sh.la[k] = P.LpT[(int64_t)k * P.ldL + a];
-        __syncthreads();
-        for (int k = tid; k < np; k += blockDim.x) sh.va[k] = dmul(k, sh.la, sh.dval, sh.eval, f);
-        __syncthreads();
-        uint64_t part = 0;
-        for (int k = tid; k < np; k += blockDim.x) part += fp_mul(sh.la[k], sh.va[k], f);
-        uint32_t caa = fp_sub(s_at(P.S, P.ldS, a, a), fp_reduce64(block_sum(part, sh.red), f), f);
+        const uint32_t W = sh.W;
+        for (int k = tid; k < np; k += NCT) sh.za[k] = zval(k, sh.U + a, SSTRIDE, sh, f);
+        cbar();
+        // c~_a[t] for the window rows t >= a (t = a included)
+        const uint32_t ca_t = schur2<BIG>(P, sh.U, lr, lr, a, W, sh.za, np, half, inwin && lr >= a, true);
+        if (lr == a && half == 0) sh.caa = ca_t;
+        cbar();
+        lap(0);
+        const uint32_t caa = sh.caa;
 
         if (caa != 0) {
-            // ---- 1x1 pivot ----
-            uint32_t dinv = fp_inv(caa, f);
-            if (helpers) publish(P, sh, EV_PIVOT1, a, -1, np, dinv, 0, 0);
-            {
-                const int t = tid;  // window rows: one per thread (w <= W0 == blockDim.x)
-                if (t >= a && t < w) {
-                    uint32_t c = schur_entry(P, t, a, sh.va, np);
-                    P.LpT[(int64_t)np * P.ldL + t] = fp_mul(c, dinv, f);
-                }
+            // ---- 1x1 pivot: U~[:, np] = c~_a, delta = W c~_a[a] ----
+            if (inwin && lr >= a && half == 0) {
+                sh.U[np * SSTRIDE + lr] = ca_t;
+                P.LpT[(int64_t)np * P.ldL + lr] = ca_t;
             }
-            __syncthreads();
+            const uint32_t delta = fp_mul(W, caa, f);
+            for (int k = tid; k < np; k += NCT)
+                if (sh.kind[k] != K_2B) sh.bw[k] = fp_mul(sh.bw[k], delta, f);
+            if (helpers) push_event(EV_PIVOT1, a, -1, np, W, 0, sh.za, nullptr, nullptr, np);
             if (tid == 0) {
-                sh.piv_rows[np] = a; sh.dval[np] = caa; sh.eval[np] = 0;
+                sh.kind[np] = K_1x1; sh.bw[np] = W; sh.piv[np] = caa; sh.w0[np] = W;
+                sh.W = fp_mul(W, delta, f);
+                sh.piv_rows[np] = a;
                 sh.wstate[a] = 1; sh.np = np + 1; sh.ia = ia + 1;
             }
-            __syncthreads();
+            cbar();
+            lap(2);
             continue;
         }
 
-        // ---- first non-zero of row a beyond a, inside the window ----
-        uint32_t ca_t = 0;  // c_a[t] for the thread's window row t (one row per thread)
-        int firstnz = INT_MAX;
-        {
-            const int t = tid;
-            if (t > a && t < w) {
-                ca_t = schur_entry(P, t, a, sh.va, np);
-                if (ca_t != 0) firstnz = t;
-            }
-        }
-        int b = block_min(firstnz, sh.redi);
+        // ---- first non-zero of row a beyond a inside the window ----
+        int firstnz = (half == 0 && inwin && lr > a && ca_t != 0) ? lr : INT_MAX;
+        for (int o = 16; o > 0; o >>= 1) firstnz = min(firstnz, __shfl_xor_sync(0xffffffffu, firstnz, o));
+        if (lane == 0) sh.redi[warp] = firstnz;
+        cbar();
+        int b = INT_MAX;
+        for (int i = 0; i < NCW; ++i) b = min(b, sh.redi[i]);
+        cbar();
+        lap(3);
         bool far = false;
         if (b == INT_MAX && helpers) {
             // ---- far scan over the helpers' rows ----
             const int scan_id = sh.nscan;
-            publish(P, sh, EV_SCAN, a, -1, np, 0, 0, scan_id);
+            push_event(EV_SCAN, a, -1, np, W, scan_id, sh.za, nullptr, nullptr, np);
+            lap(4);
             if (tid == 0) {
                 const int target = (scan_id + 1) * (int)(gridDim.x - 1);
                 volatile int *done = &P.sync->scan_done;
                 volatile int *ab = &P.sync->abort;
-                int64_t t0 = gtime();
+                const int64_t t0 = gtime();
                 int ok = 0;
                 for (;;) {
                     if (*done >= target) { ok = 1; break; }
@@ -304,91 +474,160 @@ __device__ void leader_loop(const PanelParams &P, bool helpers)
                 __threadfence();
                 int best = INT_MAX, owner = -1;
                 if (ok) {
-                    for (int c = 1; c < (int)gridDim.x; ++c) {
-                        int v = __ldcg(&P.scan_min[c]);
-                        if (v < best) { best = v; owner = c; }
+                    const int v = __ldcg(&P.scan_min[scan_id]);
+                    if (v >= P.w && v < P.m) {
+                        best = v;
+                        const int nh = gridDim.x - 1;
+                        const int chunk = (P.m - P.w + nh - 1) / nh;
+                        owner = 1 + (v - P.w) / chunk;
                     }
                 } else {
                     sh.abort = 1;
                 }
                 sh.b = best;
-                sh.redi[0] = owner;
+                sh.owner = owner;
                 sh.nscan = scan_id + 1;
             }
-            __syncthreads();
+            cbar();
+            lap(5);
             if (sh.abort) break;
             b = sh.b;
-            const int owner = sh.redi[0];
             if (b != INT_MAX) {
                 far = true;
-                for (int k = tid; k < np; k += blockDim.x)
-                    sh.lb[k] = __ldcg(&P.partner_lp[(int64_t)owner * KP_MAX + k]);
+                for (int k = tid; k < np; k += NCT)
+                    sh.ub[k] = __ldcg(&P.partner_lp[(int64_t)sh.owner * KP_MAX + k]);
             }
-            __syncthreads();
+            cbar();
         }
         if (b == INT_MAX) {
             // ---- zero row ----
-            __syncthreads();
             if (tid == 0) {
                 sh.zero_rows[sh.nzero] = a; sh.zero_np[sh.nzero] = np; sh.nzero += 1;
                 sh.wstate[a] = 1; sh.ia = ia + 1;
             }
-            __syncthreads();
+            cbar();
+            lap(6);
             continue;
         }
 
         // ---- 2x2 pivot on (a, b) ----
         if (!far)
-            for (int k = tid; k < np; k += blockDim.x) sh.lb[k] = P.LpT[(int64_t)k * P.ldL + b];
-        __syncthreads();
-        for (int k = tid; k < np; k += blockDim.x) sh.vb[k] = dmul(k, sh.lb, sh.dval, sh.eval, f);
-        __syncthreads();
-        uint64_t px = 0, py = 0;
-        for (int k = tid; k < np; k += blockDim.x) {
-            px += fp_mul(sh.lb[k], sh.va[k], f);
-            py += fp_mul(sh.lb[k], sh.vb[k], f);
-        }
-        uint32_t x = fp_sub(s_at(P.S, P.ldS, a, b), fp_reduce64(block_sum(px, sh.red), f), f);
-        uint32_t y = fp_sub(s_at(P.S, P.ldS, b, b), fp_reduce64(block_sum(py, sh.red), f), f);
-        uint32_t xinv = fp_inv(x, f);
-        uint32_t delta = (f.p == 2) ? y : fp_mul(y, f.inv2, f);
-        if (helpers) publish(P, sh, EV_PIVOT2, a, b, np, xinv, delta, 0);
-        {
-            const int t = tid;
-            if (t >= a && t < w) {
-            const uint32_t ca = (t == a) ? 0u : ca_t;  // c_a[a] = 0 (no 1x1 pivot)
-            uint32_t cb = schur_entry(P, t, b, sh.vb, np);
-            uint32_t beta = fp_mul(ca, xinv, f);
-            uint32_t alpha = fp_mul(fp_sub(cb, fp_mul(beta, delta, f), f), xinv, f);
-            P.LpT[(int64_t)np * P.ldL + t] = alpha;
-            P.LpT[(int64_t)(np + 1) * P.ldL + t] = beta;
+            for (int k = tid; k < np; k += NCT) sh.ub[k] = sh.U[k * SSTRIDE + b];
+        cbar();
+        for (int k = tid; k < np; k += NCT) sh.zb[k] = zval(k, sh.ub, 1, sh, f);
+        cbar();
+        // x~ = W S(a,b) - U~[b] . z_a ;  y~ = W S(b,b) - U~[b] . z_b   (warp 0)
+        if (warp == 0) {
+            uint64_t ax = 0, ay = 0;
+            for (int k = lane; k < np; k += 32) {
+                mac<true>(ax, sh.ub[k], sh.za[k], f);
+                mac<true>(ay, sh.ub[k], sh.zb[k], f);
+            }
+            uint64_t sx = fp_reduce64(ax, f), sy = fp_reduce64(ay, f);
+            for (int o = 16; o > 0; o >>= 1) {
+                sx += __shfl_xor_sync(0xffffffffu, sx, o);
+                sy += __shfl_xor_sync(0xffffffffu, sy, o);
+            }
+            if (lane == 0) {
+                sh.xy[0] = fp_sub(fp_mul(W, s_at(P.S, P.ldS, a, b), f), fp_reduce64(sx, f), f);
+                sh.xy[1] = fp_sub(fp_mul(W, s_at(P.S, P.ldS, b, b), f), fp_reduce64(sy, f), f);
             }
         }
-        __syncthreads();
+        // c~_b[t] for the window rows t >= a (overlaps warp 0's work)
+        const uint32_t cb_t = schur2<BIG>(P, sh.U, lr, lr, b, W, sh.zb, np, half, inwin && lr >= a, true);
+        cbar();
+        const uint32_t x = sh.xy[0], y = sh.xy[1];
+        if (inwin && lr >= a && half == 0) {
+            sh.U[np * SSTRIDE + lr] = ca_t;  // c~_a[a] = 0 here
+            sh.U[(np + 1) * SSTRIDE + lr] = cb_t;
+            P.LpT[(int64_t)np * P.ldL + lr] = ca_t;
+            P.LpT[(int64_t)(np + 1) * P.ldL + lr] = cb_t;
+        }
+        const uint32_t delta = fp_mul(W, fp_mul(x, x, f), f);
+        for (int k = tid; k < np; k += NCT)
+            if (sh.kind[k] != K_2B) sh.bw[k] = fp_mul(sh.bw[k], delta, f);
+        if (helpers) push_event(EV_PIVOT2, a, b, np, W, 0, sh.za, sh.zb, nullptr, np);
         if (tid == 0) {
+            sh.kind[np] = K_2A; sh.kind[np + 1] = K_2B;
+            sh.bw[np] = W; sh.mx[np] = x; sh.my[np] = y; sh.piv[np] = x; sh.w0[np] = W;
+            sh.W = fp_mul(W, delta, f);
             sh.piv_rows[np] = a; sh.piv_rows[np + 1] = b;
-            sh.dval[np] = 0; sh.dval[np + 1] = (f.p == 2) ? y : 0;
-            sh.eval[np] = x; sh.eval[np + 1] = 0;
             sh.wstate[a] = 1;
             if (b < w) sh.wstate[b] = 1;
             P.consumed[b] = 1;
             sh.np = np + 2; sh.ia = ia + 1;
         }
-        __syncthreads();
+        cbar();
+        lap(7);
     }
 
-    if (helpers && !sh.abort) publish(P, sh, EV_END, -1, -1, 0, 0, 0, 0);
+    // ---- end of panel: batch inversion, true D and the L coefficients ----
+    const int np = sh.np, iend = sh.ia, nzero = sh.nzero;
+    if (!sh.abort) {
+        if (tid == 0) {
+            // values to invert: per block, its pivot value and its W; Montgomery's trick
+            int nv = 0;
+            for (int j = 0; j < np; ++j)
+                if (sh.kind[j] != K_2B) { sh.bi[nv++] = sh.piv[j]; sh.bi[nv++] = sh.w0[j]; }
+            uint32_t run = 1;
+            for (int i = 0; i < nv; ++i) { run = fp_mul(run, sh.bi[i], f); sh.bpre[i] = run; }
+            uint32_t inv = nv ? fp_inv(run, f) : 1u;
+            for (int i = nv - 1; i >= 0; --i) {
+                const uint32_t before = i ? sh.bpre[i - 1] : 1u;
+                const uint32_t vi = sh.bi[i];
+                sh.bi[i] = fp_mul(inv, before, f);  // inverse of value i
+                inv = fp_mul(inv, vi, f);
+            }
+            // coefficients per column
+            int v = 0;
+            for (int j = 0; j < np; ++j) {
+                const uint8_t kd = sh.kind[j];
+                if (kd == K_1x1) {
+                    const uint32_t ipiv = sh.bi[v], iw0 = sh.bi[v + 1];
+                    v += 2;
+                    sh.cA[j] = ipiv;
+                    sh.cB[j] = 0;
+                    sh.dtrue[j] = fp_mul(sh.piv[j], iw0, f);
+                    sh.etrue[j] = 0;
+                } else if (kd == K_2A) {
+                    const uint32_t ix = sh.bi[v], iw0 = sh.bi[v + 1];
+                    v += 2;
+                    const uint32_t yt = sh.my[j];
+                    const uint32_t dl = (f.p == 2) ? yt : fp_mul(yt, f.inv2, f);
+                    sh.cA[j] = ix;
+                    sh.cB[j] = fp_sub(0, fp_mul(dl, fp_mul(ix, ix, f), f), f);
+                    sh.cA[j + 1] = ix;
+                    sh.cB[j + 1] = 0;
+                    sh.dtrue[j] = 0;
+                    sh.dtrue[j + 1] = (f.p == 2) ? fp_mul(yt, iw0, f) : 0u;
+                    sh.etrue[j] = fp_mul(sh.mx[j], iw0, f);
+                    sh.etrue[j + 1] = 0;
+                    ++j;
+                }
+            }
+        }
+        cbar();
+        if (helpers) {
+            __shared__ uint32_t kinds32[KP_MAX];
+            for (int k = tid; k < np; k += NCT) kinds32[k] = sh.kind[k];
+            cbar();
+            push_event(EV_END, -1, -1, np, 0, 0, kinds32, sh.cA, sh.cB, np);
+        }
+        // rewrite the window rows as true L columns
+        for (int t = tid; t < w; t += NCT) finish_row(P, sh.U + t, SSTRIDE, P.LpT + t, np, sh.kind, sh.cA, sh.cB);
+    }
+    cbar();
+    if (tid == 0) { __threadfence_block(); sh.quit = 1; }
     __threadfence();
-    __syncthreads();
+    cbar();
 
     // ---- report ----
-    const int np = sh.np, iend = sh.ia, nzero = sh.nzero;
-    for (int k = tid; k < np; k += blockDim.x) {
+    for (int k = tid; k < np; k += NCT) {
         P.out->piv_rows[k] = sh.piv_rows[k];
-        P.out->dval[k] = sh.dval[k];
-        P.out->eval[k] = sh.eval[k];
+        P.out->dval[k] = sh.dtrue[k];
+        P.out->eval[k] = sh.etrue[k];
     }
-    for (int q = tid; q < nzero; q += blockDim.x) {
+    for (int q = tid; q < nzero; q += NCT) {
         P.out->zero_rows[q] = sh.zero_rows[q];
         P.out->zero_np[q] = sh.zero_np[q];
     }
@@ -396,23 +635,20 @@ __device__ void leader_loop(const PanelParams &P, bool helpers)
     // ---- compaction of the remaining rows [iend, m) minus consumed partners ----
     const int m = P.m;
     const int len = m - iend;
-    const int per = (len + blockDim.x - 1) / blockDim.x;
+    const int per = (len + NCT - 1) / NCT;
     const int lo = iend + tid * per, hi = min(m, lo + per);
     int cnt = 0;
     for (int t = lo; t < hi; ++t) cnt += P.consumed[t] ? 0 : 1;
-    // exclusive scan of cnt over the CTA
     int incl = cnt;
-    const int lane = tid & 31, wid = tid >> 5;
     for (int o = 1; o < 32; o <<= 1) {
-        int v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
+        const int vv = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += vv;
     }
-    __syncthreads();
-    if (lane == 31) sh.redi[wid] = incl;
-    __syncthreads();
+    if (lane == 31) sh.redi[warp] = incl;
+    cbar();
     int woff = 0, total = 0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
-        if (i < wid) woff += sh.redi[i];
+    for (int i = 0; i < NCW; ++i) {
+        if (i < warp) woff += sh.redi[i];
         total += sh.redi[i];
     }
     int pos = woff + incl - cnt;
@@ -430,21 +666,25 @@ __device__ void leader_loop(const PanelParams &P, bool helpers)
         P.out->m_next = total;
         P.out->abort = sh.abort | *((volatile int *)&P.sync->abort);
         P.out->nscan = sh.nscan;
+        for (int i = 0; i < 8; ++i) P.out->cyc[i] = cyc[i];
     }
 }
 
-__global__ void __launch_bounds__(PANEL_THREADS) panel_kernel(PanelParams P)
+template <bool BIG>
+__global__ void __launch_bounds__(BLOCK, 1) panel_kernel(PanelParams P)
 {
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    Shared &sh = *reinterpret_cast<Shared *>(smem_raw);
     const bool helpers = gridDim.x > 1;
     if (blockIdx.x == 0) {
-        leader_loop(P, helpers);
+        leader_cta<BIG>(P, sh, helpers);
     } else {
         const int nh = gridDim.x - 1;
         const int far = P.m - P.w;
         const int chunk = (far + nh - 1) / nh;
         const int lo = P.w + (blockIdx.x - 1) * chunk;
         const int hi = min(P.m, lo + chunk);
-        helper_loop(P, lo, hi);
+        helper_cta<BIG>(P, sh, lo, hi);
     }
 }
 
@@ -454,8 +694,11 @@ cudaError_t launch_panel(const PanelParams &pp, int grid, cudaStream_t st)
 {
     PanelParams p = pp;
     void *args[] = {&p};
-    if (grid <= 1)
-        return cudaLaunchKernel((const void *)panel_kernel, dim3(1), dim3(PANEL_THREADS), args, 0, st);
-    return cudaLaunchCooperativeKernel((const void *)panel_kernel, dim3(grid), dim3(PANEL_THREADS),
-                                       args, 0, st);
+    const bool big = pp.f.p >= (1u << 28);
+    const void *fn = big ? (const void *)panel_kernel<true> : (const void *)panel_kernel<false>;
+    const size_t smem = sizeof(Shared);
+    cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    if (grid <= 1) return cudaLaunchKernel(fn, dim3(1), dim3(BLOCK), args, smem, st);
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(BLOCK), args, smem, st);
 }

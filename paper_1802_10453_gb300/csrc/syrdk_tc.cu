@@ -35,12 +35,15 @@ namespace {
 
 constexpr int BM = 128;            // rows per output tile (MMA M)
 constexpr int KST = 64;            // K' elements per pipeline stage
-constexpr int NST = 3;             // pipeline stages
+
 constexpr int STAGE_A = BM * KST * 2;        // 16 KB
 constexpr int STAGE_B_MAX = 256 * KST * 2;   // 32 KB
 constexpr int STAGE_BYTES = STAGE_A + STAGE_B_MAX;
-constexpr int EPI_THREADS = 128;
-constexpr int TC_THREADS = 192;
+constexpr int EPI_WARPS = 8;       // two warps per TMEM lane quarter, each half the columns
+constexpr int EPI_THREADS = EPI_WARPS * 32;
+constexpr int TC_THREADS = 64 + EPI_THREADS;
+
+__host__ __device__ constexpr int nst_for(int bn) { return bn <= 64 ? 4 : 3; }
 
 // ---------------------------------------------------------------------------
 // PTX wrappers
@@ -207,15 +210,17 @@ struct TcArgs {
     int32_t *status;
     TileMap tm;
     int ntiles;
+    int nst;
 };
 
 __global__ void __launch_bounds__(TC_THREADS, 1) syrdk_tc_kernel(const TcArgs args)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int NST = args.nst;
     uint8_t *stages = smem;
     uint32_t *stage_out = (uint32_t *)(smem + NST * STAGE_BYTES);  // [BM][bn + 1]
-    uint64_t *bars = (uint64_t *)(smem + NST * STAGE_BYTES + BM * (128 + 1) * 4);
+    uint64_t *bars = (uint64_t *)(smem + NST * STAGE_BYTES + BM * (args.bn + 1) * 4);
     // bars[0..NST) full, [NST..2NST) empty, [2NST, 2NST+2) tmem full,
     // [2NST+2, 2NST+4) tmem empty, [2NST+4] drain
     uint32_t *tmem_holder = (uint32_t *)(bars + 2 * NST + 5);
@@ -328,11 +333,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) syrdk_tc_kernel(const TcArgs ar
         }
     } else {
         // ---------------- epilogue ----------------
+        const int ew = warp - 2;             // 0..7
         const int q = warp & 3;              // TMEM lane quarter this warp may access
+        const int hcol = ew >> 2;            // which half of the tile's columns
         const int row = q * 32 + lane;       // tile row owned in the TMEM phase
         const int bn = args.bn;
         const int ldo = bn + 1;
+        const int cw = bn / 2;               // columns per warp
         const FieldP f = args.f;
+        const int L = args.limbs;
+        const uint64_t bias = args.bias;
         uint32_t tcount = 0;
         for (int t = blockIdx.x; t < args.ntiles; t += gridDim.x, ++tcount) {
             int I, J;
@@ -345,39 +355,40 @@ __global__ void __launch_bounds__(TC_THREADS, 1) syrdk_tc_kernel(const TcArgs ar
             }
             tc_fence_after();
             const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + buf * (uint32_t)np_;
-            for (int j0 = 0; j0 < bn; j0 += 16) {
-                int64_t val[16];
+            for (int j0 = hcol * cw; j0 < (hcol + 1) * cw; j0 += 16) {
+                uint32_t r[4][16];
+                tmem_ld16(tbase + (uint32_t)(0 * bn + j0), r[0]);
+                if (L > 1) tmem_ld16(tbase + (uint32_t)(1 * bn + j0), r[1]);
+                if (L > 2) tmem_ld16(tbase + (uint32_t)(2 * bn + j0), r[2]);
+                if (L > 3) tmem_ld16(tbase + (uint32_t)(3 * bn + j0), r[3]);
+                tmem_wait_ld();
+                uint32_t *dst = stage_out + row * ldo + j0;
 #pragma unroll
-                for (int e = 0; e < 16; ++e) val[e] = 0;
-                for (int v = 0; v < args.limbs; ++v) {
-                    uint32_t r[16];
-                    tmem_ld16(tbase + (uint32_t)(v * bn + j0), r);
-                    tmem_wait_ld();
-                    const int64_t w = (int64_t)1 << (8 * v);
-#pragma unroll
-                    for (int e = 0; e < 16; ++e) val[e] += (int64_t)__float2int_rn(__uint_as_float(r[e])) * w;
+                for (int e = 0; e < 16; ++e) {
+                    int64_t v = (int64_t)__float2int_rn(__uint_as_float(r[0][e]));
+                    if (L > 1) v += (int64_t)__float2int_rn(__uint_as_float(r[1][e])) << 8;
+                    if (L > 2) v += (int64_t)__float2int_rn(__uint_as_float(r[2][e])) << 16;
+                    if (L > 3) v += (int64_t)__float2int_rn(__uint_as_float(r[3][e])) << 24;
+                    dst[e] = fp_reduce64((uint64_t)(v + (int64_t)bias), f);
                 }
-#pragma unroll
-                for (int e = 0; e < 16; ++e)
-                    stage_out[row * ldo + j0 + e] = fp_reduce64((uint64_t)(val[e] + (int64_t)args.bias), f);
             }
             tc_fence_before();
             mbar_arrive(smem_u32(&bars[2 * NST + 2 + buf]));
-            asm volatile("bar.sync 1, 128;" ::: "memory");
+            asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");
             // coalesced read-modify-write of the Schur complement
-            const int ew = (warp - 2);  // 0..3
-            for (int rr = ew; rr < BM; rr += 4) {
+            for (int rr = ew; rr < BM; rr += EPI_WARPS) {
                 const int i = I * BM + rr;
                 if (i >= args.m_next) break;
                 const uint32_t *srow = args.S + (int64_t)__ldg(args.sigma + i) * args.ldS;
                 uint32_t *drow = args.Snext + (int64_t)i * args.ldS;
+                const uint32_t *sres = stage_out + rr * ldo;
                 for (int jj = lane; jj < bn; jj += 32) {
                     const int j = J * bn + jj;
                     if (j > i || j >= args.m_next) continue;
-                    drow[j] = fp_sub(__ldg(srow + __ldg(args.sigma + j)), stage_out[rr * ldo + jj], f);
+                    drow[j] = fp_sub(__ldg(srow + __ldg(args.sigma + j)), sres[jj], f);
                 }
             }
-            asm volatile("bar.sync 1, 128;" ::: "memory");
+            asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");
         }
     }
 
@@ -565,7 +576,8 @@ cudaError_t launch_syrdk_tc(const uint32_t *S, int64_t ldS, const int *sigma, in
     a.tm.nfull = a.tm.c * (nI - 1) * nI / 2;
     a.tm.nlast = (m_next + a.bn - 1) / a.bn;
     a.ntiles = a.tm.nfull + a.tm.nlast;
-    const size_t smem = 1024 + (size_t)NST * STAGE_BYTES + (size_t)BM * (128 + 1) * 4 + 128;
+    a.nst = nst_for(a.bn);
+    const size_t smem = 1024 + (size_t)a.nst * STAGE_BYTES + (size_t)BM * (a.bn + 1) * 4 + 256;
     cudaError_t err = cudaFuncSetAttribute(syrdk_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     int grid = a.ntiles < num_sms ? a.ntiles : num_sms;
