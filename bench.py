@@ -307,8 +307,8 @@ def main():
     phases = {"pivot_chain_ms": prof[0] / args.steps, "operand_prep_ms": prof[1] / args.steps,
               "syrdk_ms": syrdk_ms, "panels": prof[6] / args.steps, "far_scans": prof[7] / args.steps,
               "leader_ms": {k: prof[8 + i] / args.steps / (clocks.get("sm_mhz") or 2070.0) / 1e3
-                            for i, k in enumerate(["cand_column", "inv_wait", "store_1x1", "search",
-                                                   "scan_push", "scan_wait", "zero_row", "pivot_2x2"])}}
+                            for i, k in enumerate(["cand_column", "rollback", "store_1x1", "search",
+                                                   "spec_scan", "scan_wait", "zero_row", "pivot_2x2"])}}
 
     # end to end through the public API with host buffers
     e2e = None

@@ -12,7 +12,10 @@ constexpr int KP_MAX = 128;
 constexpr int W0 = 256;
 constexpr int ROWS_PER_HELPER = 256;  // far rows per helper CTA kept in shared memory
 constexpr int PANEL_THREADS_V2 = 576; // 16 compute warps (two threads per row) + 2 service warps
-constexpr int MAX_EVENTS = 2 * W0 + 4;
+constexpr int MAX_EVENTS = 8192;      // events per panel (a panel ends early at the cap)
+constexpr int MAX_SCANS = 4096;       // far scans per panel
+constexpr int PARTNER_RING = 64;      // per-scan partner-row buffers
+constexpr int MAX_PANEL_GRID = 256;
 constexpr int EV_WORDS = 4 * KP_MAX;  // payload words per event
 
 // Row storage of the Schur complement and of L: leading dimension rounded up so
@@ -35,9 +38,16 @@ struct Event {
 // Counters the CTAs of one panel launch share (zeroed before the launch).
 struct PanelSync {
     int ev_count;    // events published by the leader
-    int scan_done;   // helper CTAs that answered scans, cumulative
+    int scan_done;   // unused
     int abort;       // set by whoever times out
     int pad;
+};
+
+// Answer to one far scan: helpers lower `min` to their first non-zero row and
+// then count themselves in `done` (initialised to done = 0, min = INT_MAX).
+struct ScanSlot {
+    int done;
+    int min;
 };
 
 // What the panel kernel reports back to the host.
@@ -74,8 +84,8 @@ struct PanelParams {
     PanelSync *sync;
     Event *events;
     uint32_t *evvec;        // [MAX_EVENTS][EV_WORDS]
-    int *scan_min;          // [MAX_EVENTS]: first non-zero row of each far scan (atomicMin)
-    uint32_t *partner_lp;   // [gridDim.x][KP_MAX]
+    ScanSlot *scans;        // [MAX_SCANS]
+    uint32_t *partner_lp;   // [PARTNER_RING][MAX_PANEL_GRID][KP_MAX]: candidate rows per scan
     int64_t budget_ns;
     int32_t *status;
 };

@@ -108,7 +108,7 @@ int fp64_kred(uint32_t p)
 struct Layout {
     int64_t ldS;
     size_t S0, S1, Lw, LpT, idx0, idx1, sigma, consumed, piv_all, d_all, e_all, zero_all, zero_cols;
-    size_t out, sync, events, evvec, scan_min, partner_lp, opA, opB, total;
+    size_t out, sync, events, evvec, scans, partner_lp, opA, opB, total;
 };
 
 constexpr int MAX_GRID = 1024;
@@ -141,8 +141,8 @@ int make_layout(int64_t n, uint32_t p, int path, Layout &L)
     L.sync = take(sizeof(PanelSync));
     L.events = take((size_t)MAX_EVENTS * sizeof(Event));
     L.evvec = take((size_t)MAX_EVENTS * EV_WORDS * 4);
-    L.scan_min = take((size_t)MAX_EVENTS * 4);
-    L.partner_lp = take((size_t)MAX_GRID * KP_MAX * 4);
+    L.scans = take((size_t)MAX_SCANS * sizeof(ScanSlot));
+    L.partner_lp = take((size_t)PARTNER_RING * MAX_PANEL_GRID * KP_MAX * 4);
     if (path == LDLT_PATH_FP64) {
         L.opA = take(fp64_operand_bytes(nn));
         L.opB = L.opA;  // GT follows GDT inside the same allocation
@@ -264,7 +264,7 @@ extern "C" int ldlt_rpm_factor(int64_t n, uint32_t p, uint32_t *A, int64_t lda, 
         CK(cudaMemset2DAsync(LpT, (size_t)ldS * 4, 0, (size_t)m * 4, KP_MAX, st));
         CK(cudaMemsetAsync(consumed, 0, (size_t)m, st));
         CK(cudaMemsetAsync(sync, 0, sizeof(PanelSync), st));
-        CK(cudaMemsetAsync(w + Lo.scan_min, 0x7F, (size_t)MAX_EVENTS * 4, st));  // "no hit" > any row
+
         PanelParams pp;
         pp.S = Sbuf[cur]; pp.ldS = ldS; pp.m = m; pp.f = f;
         pp.kp = KP_MAX; pp.w = m < W0 ? m : W0;
@@ -272,13 +272,13 @@ extern "C" int ldlt_rpm_factor(int64_t n, uint32_t p, uint32_t *A, int64_t lda, 
         pp.consumed = consumed; pp.idx = idxb[cur]; pp.sigma = sigma; pp.idx_next = idxb[cur ^ 1];
         pp.out = out; pp.sync = sync;
         pp.events = (Event *)(w + Lo.events); pp.evvec = (uint32_t *)(w + Lo.evvec);
-        pp.scan_min = (int *)(w + Lo.scan_min); pp.partner_lp = (uint32_t *)(w + Lo.partner_lp);
+        pp.scans = (ScanSlot *)(w + Lo.scans); pp.partner_lp = (uint32_t *)(w + Lo.partner_lp);
         pp.budget_ns = g_budget_ns; pp.status = status;
         int grid = 1;
         if (m > pp.w) {
             const int need = 1 + (m - pp.w + ROWS_PER_HELPER - 1) / ROWS_PER_HELPER;
             grid = need < nsm ? need : nsm;
-            if (grid > MAX_GRID) grid = MAX_GRID;
+            if (grid > MAX_PANEL_GRID) grid = MAX_PANEL_GRID;
         }
         if (prof) CK(cudaEventRecord(ev[0], st));
         CK(launch_panel(pp, grid, st));

@@ -90,6 +90,9 @@ __device__ __forceinline__ void mac(uint64_t &acc, uint32_t a, uint32_t b, const
     if (BIG) acc -= (acc >> 63) * f.m63;
 }
 
+constexpr int NPEND = 16;                     // speculative far scans in flight
+constexpr int SRING = 128;                    // posted scan results
+
 struct Shared {
     uint32_t U[KP_MAX * SSTRIDE];      // U~ columns of this CTA's rows, k-major
     uint32_t ring[NSLOT][EV_WORDS];    // event payloads
@@ -108,14 +111,27 @@ struct Shared {
     int zero_rows[W0];
     int zero_np[W0];
     uint8_t wstate[W0];
+    // speculative far scans: a row whose window part is zero is taken as a
+    // zero row while its scan is in flight; a scan that finds a partner rolls
+    // the panel back to that row.
+    int pend_id[NPEND], pend_row[NPEND], pend_np[NPEND], pend_nz[NPEND];
+    uint32_t pend_W[NPEND];
+    uint32_t pend_bw[NPEND][KP_MAX];
+    int res_min[SRING];
     int redi[32];
     uint32_t xy[4];
     uint32_t caa;
     volatile int ev_ready;             // events written to the ring (leader) / fetched (helper)
     volatile int ev_done;              // events published (leader) / processed (helper)
     volatile int quit;
+    volatile int nscan_pub;            // scans published (leader -> watcher warp)
+    volatile int scan_resolved;        // scans answered by every helper (watcher -> leader)
     uint32_t W;
     int np, ia, nzero, nscan, abort, b, owner, nblk;
+    int ph, pt;                        // pending scans [ph, pt)
+    int rb, rb_b;                      // rollback request
+    int force_b, force_sid;            // partner found by a resolved scan
+    int nrollback;
 };
 
 __device__ void raise_timeout(const PanelParams &P)
@@ -192,41 +208,50 @@ __device__ void helper_cta(const PanelParams &P, Shared &sh, int lo, int hi)
     __syncthreads();
 
     if (warp == NCW) {
-        // ---- poller: fetch events into the shared ring ----
-        for (int e = 0;; ++e) {
-            int go = 0;
+        // ---- poller: fetch every published event that fits into the ring ----
+        int e = 0;
+        for (;;) {
+            int avail = 0;
             if (lane == 0) {
                 const int64_t t0 = gtime();
                 volatile int *cnt = &P.sync->ev_count;
                 volatile int *ab = &P.sync->abort;
                 for (;;) {
-                    if (*cnt > e && sh.ev_done > e - NSLOT) { go = 1; break; }
+                    const int c = *cnt;
+                    const int room = sh.ev_done + NSLOT;
+                    const int lim = c < room ? c : room;
+                    if (lim > e) { avail = lim - e; break; }
                     if (*ab) break;
                     if (gtime() - t0 > P.budget_ns) { raise_timeout(P); break; }
                 }
             }
-            go = __shfl_sync(0xffffffffu, go, 0);
-            if (!go) {
+            avail = __shfl_sync(0xffffffffu, avail, 0);
+            if (!avail) {
                 if (lane == 0) { __threadfence_block(); sh.quit = 1; }
                 return;
             }
             __threadfence();
-            const int s = e % NSLOT;
-            const int *gh = reinterpret_cast<const int *>(&P.events[e]);
-            const int hv = lane < 8 ? __ldcg(gh + lane) : 0;
-            const int kind = __shfl_sync(0xffffffffu, hv, 0);
-            const int np = __shfl_sync(0xffffffffu, hv, 3);
-            if (lane < 8) reinterpret_cast<int *>(&sh.ev[s])[lane] = hv;
-            const uint32_t *vv = P.evvec + (int64_t)e * EV_WORDS;
-            const int words = (kind == EV_END) ? 3 * KP_MAX : (kind == EV_PIVOT2 ? 2 * KP_MAX : KP_MAX);
-            for (int k = lane; k < words; k += 32) {
-                const int part = k / KP_MAX, kk = k % KP_MAX;
-                if (kind == EV_END || kk < np) sh.ring[s][k] = __ldcg(vv + (int64_t)part * KP_MAX + kk);
+            bool end = false;
+            for (int q = 0; q < avail; ++q) {
+                const int ee = e + q, s = ee % NSLOT;
+                const int *gh = reinterpret_cast<const int *>(&P.events[ee]);
+                const int hv = lane < 8 ? __ldcg(gh + lane) : 0;
+                const int kind = __shfl_sync(0xffffffffu, hv, 0);
+                const int np = __shfl_sync(0xffffffffu, hv, 3);
+                if (lane < 8) reinterpret_cast<int *>(&sh.ev[s])[lane] = hv;
+                const uint32_t *vv = P.evvec + (int64_t)ee * EV_WORDS;
+                const int words = (kind == EV_END) ? 3 * KP_MAX : (kind == EV_PIVOT2 ? 2 * KP_MAX : KP_MAX);
+                for (int k = lane; k < words; k += 32) {
+                    const int kk = k % KP_MAX;
+                    if (kind == EV_END || kk < np) sh.ring[s][k] = __ldcg(vv + k);
+                }
+                end = end || (kind == EV_END);
             }
             __threadfence_block();
             __syncwarp();
-            if (lane == 0) sh.ev_ready = e + 1;
-            if (kind == EV_END) return;
+            if (lane == 0) sh.ev_ready = e + avail;
+            if (end) return;
+            e += avail;
         }
     }
     if (warp > NCW) return;  // the second service warp has no work in a helper
@@ -254,13 +279,12 @@ __device__ void helper_cta(const PanelParams &P, Shared &sh, int lo, int hi)
             const uint32_t *kinds = sh.ring[s];
             const uint32_t *cA = sh.ring[s] + KP_MAX;
             const uint32_t *cB = sh.ring[s] + 2 * KP_MAX;
-            __shared__ uint8_t kb[KP_MAX];
-            for (int k = tid; k < np; k += NCT) kb[k] = (uint8_t)kinds[k];
+            for (int k = tid; k < np; k += NCT) sh.kind[k] = (uint8_t)kinds[k];
             cbar();
             for (int lr = tid; lr < nrows; lr += NCT) {
                 const int t = lo + lr;
-                if (lr < SROWS) finish_row(P, sh.U + lr, SSTRIDE, P.LpT + t, np, kb, cA, cB);
-                else finish_row(P, P.LpT + t, (int)P.ldL, P.LpT + t, np, kb, cA, cB);
+                if (lr < SROWS) finish_row(P, sh.U + lr, SSTRIDE, P.LpT + t, np, sh.kind, cA, cB);
+                else finish_row(P, P.LpT + t, (int)P.ldL, P.LpT + t, np, sh.kind, cA, cB);
             }
             return;
         }
@@ -295,18 +319,20 @@ __device__ void helper_cta(const PanelParams &P, Shared &sh, int lo, int hi)
             cbar();
             int mn = INT_MAX;
             for (int i = 0; i < NCW; ++i) mn = min(mn, sh.redi[i]);
+            const int sid = sh.ev[s].scan_id;
             if (mn != INT_MAX) {
                 const int lr = mn - lo;
+                uint32_t *dst = P.partner_lp +
+                                ((int64_t)(sid % PARTNER_RING) * MAX_PANEL_GRID + blockIdx.x) * KP_MAX;
                 for (int k = tid; k < np; k += NCT)
-                    P.partner_lp[(int64_t)blockIdx.x * KP_MAX + k] =
-                        lr < SROWS ? sh.U[k * SSTRIDE + lr] : P.LpT[(int64_t)k * P.ldL + mn];
+                    dst[k] = lr < SROWS ? sh.U[k * SSTRIDE + lr] : P.LpT[(int64_t)k * P.ldL + mn];
             }
             __threadfence();
             cbar();
             if (tid == 0) {
-                if (mn != INT_MAX) atomicMin(&P.scan_min[sh.ev[s].scan_id], mn);
+                if (mn != INT_MAX) atomicMin(&P.scans[sid].min, mn);
                 __threadfence();
-                atomicAdd(&P.sync->scan_done, 1);
+                atomicAdd(&P.scans[sid].done, 1);
             }
         }
         cbar();
@@ -324,22 +350,28 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
     const int warp = tid >> 5, lane = tid & 31;
     const FieldP f = P.f;
     const int w = P.w;
+    const int nh = gridDim.x - 1;
     for (int t = tid; t < W0; t += blockDim.x) sh.wstate[t] = 0;
     if (tid == 0) {
         sh.np = 0; sh.ia = 0; sh.nzero = 0; sh.nscan = 0; sh.abort = 0; sh.nblk = 0;
         sh.ev_ready = 0; sh.ev_done = 0; sh.quit = 0; sh.W = 1u;
+        sh.nscan_pub = 0; sh.scan_resolved = 0; sh.ph = 0; sh.pt = 0;
+        sh.rb = -1; sh.force_b = -1; sh.force_sid = -1; sh.nrollback = 0;
     }
     __syncthreads();
 
     if (warp == NCW + 1) {
-        // ---- publisher: ring slot -> global event, fence, then the counter ----
+        // ---- publisher: every ready ring slot -> global, one fence, then the counter ----
         if (!helpers) return;
-        for (int e = 0;; ++e) {
+        int e = 0;
+        int last_scan = -1;
+        for (;;) {
             int ready = 0;
             if (lane == 0) {
                 const int64_t t0 = gtime();
                 for (;;) {
-                    if (sh.ev_ready > e) { ready = 1; break; }
+                    const int r = sh.ev_ready;
+                    if (r > e) { ready = r; break; }
                     if (sh.quit) break;
                     if (gtime() - t0 > 4 * P.budget_ns + 1000000) break;
                 }
@@ -347,55 +379,125 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
             ready = __shfl_sync(0xffffffffu, ready, 0);
             if (!ready) return;
             __threadfence_block();
-            const int s = e % NSLOT;
-            const int kind = sh.ev[s].kind, np = sh.ev[s].np;
-            uint32_t *vv = P.evvec + (int64_t)e * EV_WORDS;
-            const int words = (kind == EV_END) ? 3 * KP_MAX : (kind == EV_PIVOT2 ? 2 * KP_MAX : KP_MAX);
-            for (int k = lane; k < words; k += 32) {
-                const int kk = k % KP_MAX;
-                if (kind == EV_END || kk < np) vv[k] = sh.ring[s][k];
+            bool end = false;
+            for (int ee = e; ee < ready; ++ee) {
+                const int s = ee % NSLOT;
+                const int kind = sh.ev[s].kind, np = sh.ev[s].np;
+                uint32_t *vv = P.evvec + (int64_t)ee * EV_WORDS;
+                const int words = (kind == EV_END) ? 3 * KP_MAX : (kind == EV_PIVOT2 ? 2 * KP_MAX : KP_MAX);
+                for (int k = lane; k < words; k += 32) {
+                    const int kk = k % KP_MAX;
+                    if (kind == EV_END || kk < np) vv[k] = sh.ring[s][k];
+                }
+                if (lane < 8)
+                    reinterpret_cast<int *>(&P.events[ee])[lane] = reinterpret_cast<const int *>(&sh.ev[s])[lane];
+                if (kind == EV_SCAN && lane == 0) {
+                    P.scans[sh.ev[s].scan_id].done = 0;
+                    P.scans[sh.ev[s].scan_id].min = INT_MAX;
+                    last_scan = sh.ev[s].scan_id;
+                }
+                end = end || (kind == EV_END);
             }
-            if (lane < 8) reinterpret_cast<int *>(&P.events[e])[lane] = reinterpret_cast<const int *>(&sh.ev[s])[lane];
             __threadfence();
             __syncwarp();
             if (lane == 0) {
-                atomicExch(&P.sync->ev_count, e + 1);
-                sh.ev_done = e + 1;
+                atomicExch(&P.sync->ev_count, ready);
+                sh.ev_done = ready;
+                if (last_scan >= 0) sh.nscan_pub = last_scan + 1;  // the watcher may poll those slots now
             }
             __syncwarp();
-            if (kind == EV_END) return;
+            if (end) return;
+            e = ready;
         }
     }
-    if (warp == NCW) return;  // spare service warp
+    if (warp == NCW) {
+        // ---- watcher: posts the answers of the far scans, in order ----
+        if (!helpers) return;
+        for (int id = 0;; ++id) {
+            int go = 0, v = INT_MAX;
+            if (lane == 0) {
+                int64_t t0 = gtime();
+                for (;;) {
+                    if (sh.nscan_pub > id) { go = 1; break; }
+                    if (sh.quit) break;
+                    if (gtime() - t0 > 4 * P.budget_ns + 1000000) break;
+                }
+                if (go) {
+                    go = 0;
+                    volatile int *done = &P.scans[id].done;
+                    volatile int *ab = &P.sync->abort;
+                    t0 = gtime();
+                    for (;;) {
+                        if (*done >= nh) { go = 1; break; }
+                        if (*ab || sh.quit) break;
+                        if (gtime() - t0 > P.budget_ns) { raise_timeout(P); break; }
+                    }
+                    if (go) {
+                        __threadfence();
+                        v = __ldcg(&P.scans[id].min);
+                        sh.res_min[id % SRING] = v;
+                        __threadfence_block();
+                        sh.scan_resolved = id + 1;
+                    }
+                }
+            }
+            go = __shfl_sync(0xffffffffu, go, 0);
+            if (!go) return;
+        }
+    }
 
     // ---- compute warps: 512 threads, two per window row ----
     const int half = tid & 1;
     const int lr = tid >> 1;  // window row of this thread pair
     const bool inwin = lr < w;
 
-    // put an event in the ring: payload words are copied from `src` parts
-    auto push_event = [&](int kind, int a, int b, int np, uint32_t s0, int scan_id, const uint32_t *p0,
-                          const uint32_t *p1, const uint32_t *p2, int nwords) {
+    // Put an event in the ring.  Called by warp 0 only (all its lanes): the
+    // other warps go on, and the payload vectors are not rewritten before the
+    // next compute barrier.
+    auto push_w0 = [&](int kind, int a, int b, int np, uint32_t s0, int scan_id, const uint32_t *p0,
+                       const uint32_t *p1, const uint32_t *p2, int nwords) {
         const int e = sh.ev_ready;
-        if (tid == 0) {
+        if (lane == 0) {
             const int64_t t0 = gtime();
             while (sh.ev_done <= e - NSLOT) {
                 if (gtime() - t0 > P.budget_ns) { raise_timeout(P); sh.abort = 1; break; }
             }
         }
-        cbar();
+        __syncwarp();
         const int s = e % NSLOT;
-        for (int k = tid; k < nwords; k += NCT) {
+        for (int k = lane; k < nwords; k += 32) {
             sh.ring[s][k] = p0[k];
             if (p1) sh.ring[s][KP_MAX + k] = p1[k];
             if (p2) sh.ring[s][2 * KP_MAX + k] = p2[k];
         }
-        if (tid == 0) {
+        if (lane == 0) {
             sh.ev[s].kind = kind; sh.ev[s].a = a; sh.ev[s].b = b; sh.ev[s].np = np;
             sh.ev[s].s0 = s0; sh.ev[s].s1 = 0; sh.ev[s].scan_id = scan_id; sh.ev[s].pad = 0;
         }
-        cbar();
-        if (tid == 0) { __threadfence_block(); sh.ev_ready = e + 1; }
+        __syncwarp();
+        if (lane == 0) { __threadfence_block(); sh.ev_ready = e + 1; }
+        __syncwarp();
+    };
+    // Thread 0: take in answered scans, oldest first; a hit asks for a rollback.
+    auto check_scans = [&]() {
+        sh.rb = -1;
+        while (sh.ph < sh.pt) {
+            const int k = sh.ph;
+            const int id = sh.pend_id[k % NPEND];
+            if (sh.scan_resolved <= id) break;
+            const int v = sh.res_min[id % SRING];
+            if (v >= w && v < P.m) { sh.rb = k; sh.rb_b = v; break; }
+            sh.ph = k + 1;  // confirmed: that row is a zero row
+        }
+    };
+    // Thread 0: wait until the oldest pending scan is answered.
+    auto wait_head = [&]() {
+        const int id = sh.pend_id[sh.ph % NPEND];
+        const int64_t t0 = gtime();
+        while (sh.scan_resolved <= id) {
+            if (gtime() - t0 > P.budget_ns) { raise_timeout(P); sh.abort = 1; break; }
+        }
+        __threadfence_block();
     };
 
     long long cyc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -405,11 +507,48 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
     };
 
     for (;;) {
-        const int np = sh.np, ia = sh.ia;
-        if (np > P.kp - 2 || ia >= w || sh.abort) break;
-        if (sh.wstate[ia]) {
+        if (sh.rb >= 0) {
+            // ---- roll back to the row whose scan found a partner ----
+            const int slot = sh.rb % NPEND;
+            const int ak = sh.pend_row[slot], npk = sh.pend_np[slot];
+            const int np_cur = sh.np;
+            for (int j = tid; j < np_cur; j += NCT)
+                if (j >= npk && sh.kind[j] == K_2B) P.consumed[sh.piv_rows[j]] = 0;
+            for (int t = ak + tid; t < w; t += NCT) sh.wstate[t] = 0;
             cbar();
-            if (tid == 0) sh.ia = ia + 1;
+            for (int j = tid; j < npk; j += NCT)
+                if (sh.kind[j] == K_2B) {
+                    const int bb = sh.piv_rows[j];
+                    if (bb >= ak && bb < w) sh.wstate[bb] = 1;
+                }
+            for (int q = tid; q < (np_cur - npk) * w; q += NCT) {
+                const int j = npk + q / w, t = q % w;
+                sh.U[j * SSTRIDE + t] = 0;
+                P.LpT[(int64_t)j * P.ldL + t] = 0;
+            }
+            for (int k = tid; k < npk; k += NCT) sh.bw[k] = sh.pend_bw[slot][k];
+            if (tid == 0) {
+                sh.np = npk; sh.nzero = sh.pend_nz[slot]; sh.ia = ak; sh.W = sh.pend_W[slot];
+                sh.force_b = sh.rb_b; sh.force_sid = sh.pend_id[slot];
+                sh.pt = sh.rb;  // drop this and every later pending scan
+                sh.nrollback += 1;
+                sh.rb = -1;
+            }
+            cbar();
+            lap(1);
+            continue;
+        }
+        const int np = sh.np, ia = sh.ia;
+        if (sh.abort) break;
+        const bool full = np > P.kp - 2 || ia >= w || sh.ev_ready > MAX_EVENTS - 64 || sh.nscan > MAX_SCANS - 64;
+        if (full) {
+            if (sh.ph == sh.pt) break;  // nothing in flight: the panel is complete
+            if (tid == 0) { wait_head(); check_scans(); }
+            cbar();
+            continue;
+        }
+        if (sh.wstate[ia]) {
+            if (tid == 0) { sh.ia = ia + 1; check_scans(); }
             cbar();
             continue;
         }
@@ -417,9 +556,13 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
         const uint32_t W = sh.W;
         for (int k = tid; k < np; k += NCT) sh.za[k] = zval(k, sh.U + a, SSTRIDE, sh, f);
         cbar();
-        // c~_a[t] for the window rows t >= a (t = a included)
+        // c~_a[t] for the window rows t >= a (t = a included) and the first
+        // non-zero of row a beyond a inside the window, in one pass
         const uint32_t ca_t = schur2<BIG>(P, sh.U, lr, lr, a, W, sh.za, np, half, inwin && lr >= a, true);
         if (lr == a && half == 0) sh.caa = ca_t;
+        int firstnz = (half == 0 && inwin && lr > a && ca_t != 0) ? lr : INT_MAX;
+        for (int o = 16; o > 0; o >>= 1) firstnz = min(firstnz, __shfl_xor_sync(0xffffffffu, firstnz, o));
+        if (lane == 0) sh.redi[warp] = firstnz;
         cbar();
         lap(0);
         const uint32_t caa = sh.caa;
@@ -433,74 +576,62 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
             const uint32_t delta = fp_mul(W, caa, f);
             for (int k = tid; k < np; k += NCT)
                 if (sh.kind[k] != K_2B) sh.bw[k] = fp_mul(sh.bw[k], delta, f);
-            if (helpers) push_event(EV_PIVOT1, a, -1, np, W, 0, sh.za, nullptr, nullptr, np);
+            if (helpers && warp == 0) push_w0(EV_PIVOT1, a, -1, np, W, 0, sh.za, nullptr, nullptr, np);
             if (tid == 0) {
                 sh.kind[np] = K_1x1; sh.bw[np] = W; sh.piv[np] = caa; sh.w0[np] = W;
                 sh.W = fp_mul(W, delta, f);
                 sh.piv_rows[np] = a;
                 sh.wstate[a] = 1; sh.np = np + 1; sh.ia = ia + 1;
+                check_scans();
             }
             cbar();
             lap(2);
             continue;
         }
 
-        // ---- first non-zero of row a beyond a inside the window ----
-        int firstnz = (half == 0 && inwin && lr > a && ca_t != 0) ? lr : INT_MAX;
-        for (int o = 16; o > 0; o >>= 1) firstnz = min(firstnz, __shfl_xor_sync(0xffffffffu, firstnz, o));
-        if (lane == 0) sh.redi[warp] = firstnz;
-        cbar();
         int b = INT_MAX;
-        for (int i = 0; i < NCW; ++i) b = min(b, sh.redi[i]);
-        cbar();
-        lap(3);
         bool far = false;
+        if (sh.force_b >= 0) {
+            // partner found by this row's scan before the rollback
+            b = sh.force_b;
+            far = true;
+            const int chunk = (P.m - w + nh - 1) / nh;
+            const int owner = 1 + (b - w) / chunk;
+            const uint32_t *src = P.partner_lp +
+                                  ((int64_t)(sh.force_sid % PARTNER_RING) * MAX_PANEL_GRID + owner) * KP_MAX;
+            for (int k = tid; k < np; k += NCT) sh.ub[k] = __ldcg(src + k);
+        } else {
+            for (int i = 0; i < NCW; ++i) b = min(b, sh.redi[i]);
+        }
+        lap(3);
         if (b == INT_MAX && helpers) {
-            // ---- far scan over the helpers' rows ----
-            const int scan_id = sh.nscan;
-            push_event(EV_SCAN, a, -1, np, W, scan_id, sh.za, nullptr, nullptr, np);
-            lap(4);
+            // ---- speculative far scan: publish it and go on as if the row were zero ----
+            if (sh.pt - sh.ph >= NPEND) {
+                if (tid == 0) { wait_head(); check_scans(); }
+                cbar();
+                continue;  // the row is taken again from the top
+            }
+            const int sid = sh.nscan;
+            const int slot = sh.pt % NPEND;
+            if (warp == 0) {
+                push_w0(EV_SCAN, a, -1, np, W, sid, sh.za, nullptr, nullptr, np);
+                for (int k = lane; k < np; k += 32) sh.pend_bw[slot][k] = sh.bw[k];
+            }
             if (tid == 0) {
-                const int target = (scan_id + 1) * (int)(gridDim.x - 1);
-                volatile int *done = &P.sync->scan_done;
-                volatile int *ab = &P.sync->abort;
-                const int64_t t0 = gtime();
-                int ok = 0;
-                for (;;) {
-                    if (*done >= target) { ok = 1; break; }
-                    if (*ab) break;
-                    if (gtime() - t0 > P.budget_ns) { raise_timeout(P); break; }
-                }
-                __threadfence();
-                int best = INT_MAX, owner = -1;
-                if (ok) {
-                    const int v = __ldcg(&P.scan_min[scan_id]);
-                    if (v >= P.w && v < P.m) {
-                        best = v;
-                        const int nh = gridDim.x - 1;
-                        const int chunk = (P.m - P.w + nh - 1) / nh;
-                        owner = 1 + (v - P.w) / chunk;
-                    }
-                } else {
-                    sh.abort = 1;
-                }
-                sh.b = best;
-                sh.owner = owner;
-                sh.nscan = scan_id + 1;
+                sh.pend_id[slot] = sid; sh.pend_row[slot] = a; sh.pend_np[slot] = np;
+                sh.pend_nz[slot] = sh.nzero; sh.pend_W[slot] = W;
+                sh.pt = sh.pt + 1;
+                sh.nscan = sid + 1;
+                sh.zero_rows[sh.nzero] = a; sh.zero_np[sh.nzero] = np; sh.nzero += 1;
+                sh.wstate[a] = 1; sh.ia = ia + 1;
+                check_scans();
             }
             cbar();
-            lap(5);
-            if (sh.abort) break;
-            b = sh.b;
-            if (b != INT_MAX) {
-                far = true;
-                for (int k = tid; k < np; k += NCT)
-                    sh.ub[k] = __ldcg(&P.partner_lp[(int64_t)sh.owner * KP_MAX + k]);
-            }
-            cbar();
+            lap(4);
+            continue;
         }
         if (b == INT_MAX) {
-            // ---- zero row ----
+            // ---- zero row (no far rows to search) ----
             if (tid == 0) {
                 sh.zero_rows[sh.nzero] = a; sh.zero_np[sh.nzero] = np; sh.nzero += 1;
                 sh.wstate[a] = 1; sh.ia = ia + 1;
@@ -514,6 +645,7 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
         if (!far)
             for (int k = tid; k < np; k += NCT) sh.ub[k] = sh.U[k * SSTRIDE + b];
         cbar();
+        if (tid == 0) { sh.force_b = -1; sh.force_sid = -1; }
         for (int k = tid; k < np; k += NCT) sh.zb[k] = zval(k, sh.ub, 1, sh, f);
         cbar();
         // x~ = W S(a,b) - U~[b] . z_a ;  y~ = W S(b,b) - U~[b] . z_b   (warp 0)
@@ -546,7 +678,7 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
         const uint32_t delta = fp_mul(W, fp_mul(x, x, f), f);
         for (int k = tid; k < np; k += NCT)
             if (sh.kind[k] != K_2B) sh.bw[k] = fp_mul(sh.bw[k], delta, f);
-        if (helpers) push_event(EV_PIVOT2, a, b, np, W, 0, sh.za, sh.zb, nullptr, np);
+        if (helpers && warp == 0) push_w0(EV_PIVOT2, a, b, np, W, 0, sh.za, sh.zb, nullptr, np);
         if (tid == 0) {
             sh.kind[np] = K_2A; sh.kind[np + 1] = K_2B;
             sh.bw[np] = W; sh.mx[np] = x; sh.my[np] = y; sh.piv[np] = x; sh.w0[np] = W;
@@ -556,6 +688,7 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
             if (b < w) sh.wstate[b] = 1;
             P.consumed[b] = 1;
             sh.np = np + 2; sh.ia = ia + 1;
+            check_scans();
         }
         cbar();
         lap(7);
@@ -565,7 +698,7 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
     const int np = sh.np, iend = sh.ia, nzero = sh.nzero;
     if (!sh.abort) {
         if (tid == 0) {
-            // values to invert: per block, its pivot value and its W; Montgomery's trick
+            // per block: its pivot value and its W, inverted together (Montgomery's trick)
             int nv = 0;
             for (int j = 0; j < np; ++j)
                 if (sh.kind[j] != K_2B) { sh.bi[nv++] = sh.piv[j]; sh.bi[nv++] = sh.w0[j]; }
@@ -578,7 +711,6 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
                 sh.bi[i] = fp_mul(inv, before, f);  // inverse of value i
                 inv = fp_mul(inv, vi, f);
             }
-            // coefficients per column
             int v = 0;
             for (int j = 0; j < np; ++j) {
                 const uint8_t kd = sh.kind[j];
@@ -608,10 +740,9 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
         }
         cbar();
         if (helpers) {
-            __shared__ uint32_t kinds32[KP_MAX];
-            for (int k = tid; k < np; k += NCT) kinds32[k] = sh.kind[k];
+            for (int k = tid; k < np; k += NCT) sh.bpre[k] = sh.kind[k];
             cbar();
-            push_event(EV_END, -1, -1, np, 0, 0, kinds32, sh.cA, sh.cB, np);
+            if (warp == 0) push_w0(EV_END, -1, -1, np, 0, 0, sh.bpre, sh.cA, sh.cB, np);
         }
         // rewrite the window rows as true L columns
         for (int t = tid; t < w; t += NCT) finish_row(P, sh.U + t, SSTRIDE, P.LpT + t, np, sh.kind, sh.cA, sh.cB);
@@ -666,6 +797,7 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
         P.out->m_next = total;
         P.out->abort = sh.abort | *((volatile int *)&P.sync->abort);
         P.out->nscan = sh.nscan;
+        P.out->pad[0] = sh.nrollback;
         for (int i = 0; i < 8; ++i) P.out->cyc[i] = cyc[i];
     }
 }
