@@ -34,16 +34,17 @@
 namespace {
 
 constexpr int BM = 128;            // rows per output tile (MMA M)
+constexpr int BN = 64;             // output columns per tile (N' = L * BN <= 256)
+constexpr int CLD = BN + 4;        // row stride (words) of a prefetched tile of old values
 constexpr int KST = 64;            // K' elements per pipeline stage
 
 constexpr int STAGE_A = BM * KST * 2;        // 16 KB
 constexpr int STAGE_B_MAX = 256 * KST * 2;   // 32 KB
 constexpr int STAGE_BYTES = STAGE_A + STAGE_B_MAX;
-constexpr int EPI_WARPS = 8;       // two warps per TMEM lane quarter, each half the columns
+constexpr int EPI_WARPS = 8;       // two groups of four warps (one per TMEM lane quarter)
 constexpr int EPI_THREADS = EPI_WARPS * 32;
 constexpr int TC_THREADS = 64 + EPI_THREADS;
-
-__host__ __device__ constexpr int nst_for(int bn) { return bn <= 64 ? 4 : 3; }
+constexpr int NST = 3;             // pipeline stages
 
 // ---------------------------------------------------------------------------
 // PTX wrappers
@@ -217,10 +218,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) syrdk_tc_kernel(const TcArgs ar
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const int NST = args.nst;
     uint8_t *stages = smem;
-    uint32_t *stage_out = (uint32_t *)(smem + NST * STAGE_BYTES);  // [BM][bn + 1]
-    uint64_t *bars = (uint64_t *)(smem + NST * STAGE_BYTES + BM * (args.bn + 1) * 4);
+    uint32_t *cold = (uint32_t *)(smem + NST * STAGE_BYTES);  // [2 groups][BM][CLD]: old Schur values
+    uint64_t *bars = (uint64_t *)(smem + NST * STAGE_BYTES + 2 * BM * CLD * 4);
     // bars[0..NST) full, [NST..2NST) empty, [2NST, 2NST+2) tmem full,
     // [2NST+2, 2NST+4) tmem empty, [2NST+4] drain
     uint32_t *tmem_holder = (uint32_t *)(bars + 2 * NST + 5);
@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) syrdk_tc_kernel(const TcArgs ar
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_u32(&bars[2 * NST + b]), 1);
-            mbar_init(smem_u32(&bars[2 * NST + 2 + b]), EPI_THREADS);
+            mbar_init(smem_u32(&bars[2 * NST + 2 + b]), EPI_THREADS / 2);
         }
         mbar_init(smem_u32(&bars[2 * NST + 4]), 1);  // drain barrier
         *abort_flag = 0;
@@ -332,63 +332,98 @@ __global__ void __launch_bounds__(TC_THREADS, 1) syrdk_tc_kernel(const TcArgs ar
             mbar_drain(smem_u32(&bars[2 * NST + 4]), 0u, args.budget_ns);
         }
     } else {
-        // ---------------- epilogue ----------------
-        const int ew = warp - 2;             // 0..7
+        // ---------------- epilogue: two groups take alternate tiles ----------------
+        // Group g (warps 2+4g .. 5+4g) owns TMEM buffer g.  For its next tile it
+        // first gathers the old Schur values S[sigma i][sigma j] into shared
+        // memory (this overlaps the MMAs of that tile), then drains the
+        // accumulators: recombine the limbs, reduce once mod p, subtract, and
+        // store 16 consecutive columns of its row with vector stores.
+        const int g = (warp - 2) >> 2;       // group
+        const int wq = (warp - 2) & 3;       // warp within the group
         const int q = warp & 3;              // TMEM lane quarter this warp may access
-        const int hcol = ew >> 2;            // which half of the tile's columns
         const int row = q * 32 + lane;       // tile row owned in the TMEM phase
-        const int bn = args.bn;
-        const int ldo = bn + 1;
-        const int cw = bn / 2;               // columns per warp
+        uint32_t *cg = cold + g * BM * CLD;
         const FieldP f = args.f;
         const int L = args.limbs;
+        const int mn = args.m_next;
         const uint64_t bias = args.bias;
-        uint32_t tcount = 0;
-        for (int t = blockIdx.x; t < args.ntiles; t += gridDim.x, ++tcount) {
+        uint32_t tcount = g;
+        for (int t = blockIdx.x + g * gridDim.x; t < args.ntiles; t += 2 * gridDim.x, tcount += 2) {
             int I, J;
             tile_of(args.tm, t, I, J);
-            const uint32_t buf = tcount & 1u, tph = (tcount >> 1) & 1u;
-            if (!mbar_wait(smem_u32(&bars[2 * NST + buf]), tph, args.budget_ns, abort_flag)) {
+            // -- gather the old values of this tile (rows wq*32 .. wq*32+31) --
+            {
+                const int j0 = J * BN + lane, j1 = j0 + 32;
+                const int sj0 = j0 < mn ? __ldg(args.sigma + j0) : 0;
+                const int sj1 = j1 < mn ? __ldg(args.sigma + j1) : 0;
+                const int ilane = I * BM + wq * 32 + lane;
+                const int si_lane = ilane < mn ? __ldg(args.sigma + ilane) : 0;
+#pragma unroll
+                for (int r0 = 0; r0 < 32; r0 += 16) {
+                    uint32_t v0[16], v1[16];
+#pragma unroll
+                    for (int r = 0; r < 16; ++r) {
+                        const int i = I * BM + wq * 32 + r0 + r;
+                        const int si = __shfl_sync(0xffffffffu, si_lane, r0 + r);
+                        const uint32_t *srow = args.S + (int64_t)si * args.ldS;
+                        v0[r] = (i < mn && j0 <= i && j0 < mn) ? __ldg(srow + sj0) : 0u;
+                        v1[r] = (i < mn && j1 <= i && j1 < mn) ? __ldg(srow + sj1) : 0u;
+                    }
+#pragma unroll
+                    for (int r = 0; r < 16; ++r) {
+                        const int rr = wq * 32 + r0 + r;
+                        cg[rr * CLD + lane] = v0[r];
+                        cg[rr * CLD + lane + 32] = v1[r];
+                    }
+                }
+            }
+            asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory");
+            const uint32_t tph = (tcount >> 1) & 1u;
+            if (!mbar_wait(smem_u32(&bars[2 * NST + g]), tph, args.budget_ns, abort_flag)) {
                 atomicExch(args.status, LDLT_ERR_TIMEOUT_CODE);
                 *abort_flag = 1;
                 break;
             }
             tc_fence_after();
-            const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + buf * (uint32_t)np_;
-            for (int j0 = hcol * cw; j0 < (hcol + 1) * cw; j0 += 16) {
+            const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)g * (uint32_t)np_;
+            const int i = I * BM + row;
+            uint32_t *drow = args.Snext + (int64_t)i * args.ldS;
+            const uint32_t *crow = cg + row * CLD;
+#pragma unroll 1
+            for (int c0 = 0; c0 < BN; c0 += 16) {
                 uint32_t r[4][16];
-                tmem_ld16(tbase + (uint32_t)(0 * bn + j0), r[0]);
-                if (L > 1) tmem_ld16(tbase + (uint32_t)(1 * bn + j0), r[1]);
-                if (L > 2) tmem_ld16(tbase + (uint32_t)(2 * bn + j0), r[2]);
-                if (L > 3) tmem_ld16(tbase + (uint32_t)(3 * bn + j0), r[3]);
+                tmem_ld16(tbase + (uint32_t)(0 * BN + c0), r[0]);
+                if (L > 1) tmem_ld16(tbase + (uint32_t)(1 * BN + c0), r[1]);
+                if (L > 2) tmem_ld16(tbase + (uint32_t)(2 * BN + c0), r[2]);
+                if (L > 3) tmem_ld16(tbase + (uint32_t)(3 * BN + c0), r[3]);
                 tmem_wait_ld();
-                uint32_t *dst = stage_out + row * ldo + j0;
+                uint32_t o[16];
 #pragma unroll
                 for (int e = 0; e < 16; ++e) {
                     int64_t v = (int64_t)__float2int_rn(__uint_as_float(r[0][e]));
                     if (L > 1) v += (int64_t)__float2int_rn(__uint_as_float(r[1][e])) << 8;
                     if (L > 2) v += (int64_t)__float2int_rn(__uint_as_float(r[2][e])) << 16;
                     if (L > 3) v += (int64_t)__float2int_rn(__uint_as_float(r[3][e])) << 24;
-                    dst[e] = fp_reduce64((uint64_t)(v + (int64_t)bias), f);
+                    o[e] = fp_sub(crow[c0 + e], fp_reduce64((uint64_t)(v + (int64_t)bias), f), f);
+                }
+                const int jb = J * BN + c0;
+                if (i < mn) {
+                    if (jb + 15 <= i && jb + 15 < mn) {
+                        uint4 *dst = (uint4 *)(drow + jb);
+                        dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
+                        dst[1] = make_uint4(o[4], o[5], o[6], o[7]);
+                        dst[2] = make_uint4(o[8], o[9], o[10], o[11]);
+                        dst[3] = make_uint4(o[12], o[13], o[14], o[15]);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 16; ++e)
+                            if (jb + e <= i && jb + e < mn) drow[jb + e] = o[e];
+                    }
                 }
             }
             tc_fence_before();
-            mbar_arrive(smem_u32(&bars[2 * NST + 2 + buf]));
-            asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");
-            // coalesced read-modify-write of the Schur complement
-            for (int rr = ew; rr < BM; rr += EPI_WARPS) {
-                const int i = I * BM + rr;
-                if (i >= args.m_next) break;
-                const uint32_t *srow = args.S + (int64_t)__ldg(args.sigma + i) * args.ldS;
-                uint32_t *drow = args.Snext + (int64_t)i * args.ldS;
-                const uint32_t *sres = stage_out + rr * ldo;
-                for (int jj = lane; jj < bn; jj += 32) {
-                    const int j = J * bn + jj;
-                    if (j > i || j >= args.m_next) continue;
-                    drow[j] = fp_sub(__ldg(srow + __ldg(args.sigma + j)), sres[jj], f);
-                }
-            }
-            asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");
+            mbar_arrive(smem_u32(&bars[2 * NST + 2 + g]));
+            asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory");
         }
     }
 
@@ -523,7 +558,7 @@ int tc_limbs(uint32_t p)
     return -1;
 }
 
-int tc_bn(int limbs) { return limbs <= 2 ? 128 : 64; }
+int tc_bn(int limbs) { (void)limbs; return BN; }
 
 size_t tc_operand_bytes(int64_t n, int limbs)
 {
@@ -576,8 +611,8 @@ cudaError_t launch_syrdk_tc(const uint32_t *S, int64_t ldS, const int *sigma, in
     a.tm.nfull = a.tm.c * (nI - 1) * nI / 2;
     a.tm.nlast = (m_next + a.bn - 1) / a.bn;
     a.ntiles = a.tm.nfull + a.tm.nlast;
-    a.nst = nst_for(a.bn);
-    const size_t smem = 1024 + (size_t)a.nst * STAGE_BYTES + (size_t)BM * (a.bn + 1) * 4 + 256;
+    a.nst = NST;
+    const size_t smem = 1024 + (size_t)NST * STAGE_BYTES + (size_t)2 * BM * CLD * 4 + 256;
     cudaError_t err = cudaFuncSetAttribute(syrdk_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     int grid = a.ntiles < num_sms ? a.ntiles : num_sms;
