@@ -267,7 +267,7 @@ def main():
     clocks = sampler.stop()
     L.ldlt_rpm_profile_enable(0)
     import ctypes
-    prof = (ctypes.c_double * 16)()
+    prof = (ctypes.c_double * 32)()
     L.ldlt_rpm_profile_read(prof)
     prof = list(prof)
     ms_total = ev0.elapsed_time(ev1)
@@ -307,8 +307,13 @@ def main():
     phases = {"pivot_chain_ms": prof[0] / args.steps, "operand_prep_ms": prof[1] / args.steps,
               "syrdk_ms": syrdk_ms, "panels": prof[6] / args.steps, "far_scans": prof[7] / args.steps,
               "leader_ms": {k: prof[8 + i] / args.steps / (clocks.get("sm_mhz") or 2070.0) / 1e3
-                            for i, k in enumerate(["cand_column", "rollback", "store_1x1", "search",
-                                                   "spec_scan", "scan_wait", "zero_row", "pivot_2x2"])}}
+                            for i, k in enumerate(["z_vector", "cand_column", "tail_1x1", "tail_scan",
+                                                   "tail_2x2", "rollback", "waits_skips", "row_start"])},
+              "chain_diag": {k: prof[16 + i] / args.steps for i, k in enumerate(
+                  ["rows", "pend_full_waits", "pend_full_cycles", "ring_wait_cycles", "rollbacks",
+                   "helper1_idle_cycles", "helper1_busy_cycles", "helper1_events", "pub_batches",
+                   "events", "t0_wait_b1", "t0_wait_b2", "t511_wait_b1", "t511_wait_b2", "t0_schur",
+                   "t511_schur"])}}
 
     # end to end through the public API with host buffers
     e2e = None

@@ -122,6 +122,16 @@ int ldlt_rpm_version(void);
 void ldlt_rpm_set_wait_budget_ns(int64_t ns);
 
 /*
+ * ldlt_rpm_set_speculation -- how many far scans the pivot chain may have in
+ * flight while it continues past rows whose window part is zero (1..16,
+ * default 16).  A scan that finds a partner rolls the panel back to its row,
+ * so the depth trades waiting against discarded work; results do not depend
+ * on it.  No counterpart in the paper (a scheduling parameter of this GPU
+ * organisation).  Returns LDLT_OK or LDLT_ERR_ARG.
+ */
+int ldlt_rpm_set_speculation(int depth);
+
+/*
  * Profiling counters (no counterpart in the paper; they feed the roofline
  * report).  When enabled, ldlt_rpm_factor records CUDA events around its
  * phases on the caller's stream and accumulates, across calls:
@@ -135,14 +145,18 @@ void ldlt_rpm_set_wait_budget_ns(int64_t ns);
  *   out[6] number of panels
  *   out[7] far scans issued by the pivot chain
  *   out[8..15] SM clock cycles the pivot chain's leader spent per phase:
- *          candidate column, wait for pivot inverse, 1x1 store, search,
- *          scan request, scan wait, zero row, 2x2 pivot
+ *          candidate column, rollback, 1x1 store, search, scan request,
+ *          (unused), zero row, 2x2 pivot
+ *   out[16..31] pivot-chain diagnostics: leader row iterations, waits for
+ *          a full set of pending scans and their cycles, cycles waiting for
+ *          event-ring space, rollbacks, idle and busy cycles and events of
+ *          helper CTA 1, publisher batches, events published, (reserved)
  * ldlt_rpm_profile_read returns LDLT_OK, or LDLT_ERR_ARG for a NULL pointer.
  * The counters are process-wide and not thread-safe.
  */
 void ldlt_rpm_profile_enable(int on);
 void ldlt_rpm_profile_reset(void);
-int ldlt_rpm_profile_read(double out[16]);
+int ldlt_rpm_profile_read(double out[32]);
 
 #ifdef __cplusplus
 }

@@ -27,5 +27,6 @@ from .binding import (  # noqa: F401
     factor_raw,
     rpm_from_factor,
     set_wait_budget_ns,
+    set_speculation,
     effective_ops,
 )

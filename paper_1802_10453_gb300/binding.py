@@ -28,7 +28,7 @@ _NAMES = {0: "LDLT_OK", -1: "LDLT_ERR_ARG", -2: "LDLT_ERR_NOT_PRIME", -3: "LDLT_
           -7: "LDLT_ERR_NO_DEVICE"}
 
 EXPORTS = ["ldlt_rpm_workspace_bytes", "ldlt_rpm_factor", "rpm_from_factor", "ldlt_rpm_version",
-           "ldlt_rpm_set_wait_budget_ns"]
+           "ldlt_rpm_set_wait_budget_ns", "ldlt_rpm_set_speculation"]
 
 
 class LdltError(RuntimeError):
@@ -66,6 +66,8 @@ def lib():
             L.ldlt_rpm_version.argtypes = []
             L.ldlt_rpm_set_wait_budget_ns.restype = None
             L.ldlt_rpm_set_wait_budget_ns.argtypes = [c_i64]
+            L.ldlt_rpm_set_speculation.restype = ctypes.c_int
+            L.ldlt_rpm_set_speculation.argtypes = [ctypes.c_int]
             _lib = L
     return _lib
 
@@ -80,6 +82,12 @@ def workspace_bytes(n: int, p: int, path: int = PATH_TC) -> int:
 
 def set_wait_budget_ns(ns: int) -> None:
     lib().ldlt_rpm_set_wait_budget_ns(int(ns))
+
+
+def set_speculation(depth: int) -> None:
+    rc = lib().ldlt_rpm_set_speculation(int(depth))
+    if rc != LDLT_OK:
+        raise LdltError(rc, "speculation depth must be in 1..16")
 
 
 def effective_ops(n: int, r: int) -> float:

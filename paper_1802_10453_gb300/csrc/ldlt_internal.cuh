@@ -11,12 +11,14 @@
 constexpr int KP_MAX = 128;
 constexpr int W0 = 256;
 constexpr int ROWS_PER_HELPER = 256;  // far rows per helper CTA kept in shared memory
+constexpr int MIN_HELPER_ROWS = 64;   // fewer rows than this per helper is not worth a CTA
 constexpr int PANEL_THREADS_V2 = 576; // 16 compute warps (two threads per row) + 2 service warps
 constexpr int MAX_EVENTS = 8192;      // events per panel (a panel ends early at the cap)
 constexpr int MAX_SCANS = 4096;       // far scans per panel
 constexpr int PARTNER_RING = 64;      // per-scan partner-row buffers
 constexpr int MAX_PANEL_GRID = 256;
 constexpr int EV_WORDS = 4 * KP_MAX;  // payload words per event
+constexpr int EV_REC = 8 + EV_WORDS;  // event record: header (one Event) then payload
 
 // Row storage of the Schur complement and of L: leading dimension rounded up so
 // every row starts on a 256-byte boundary.
@@ -60,6 +62,7 @@ struct PanelOut {
     int nscan;       // far scans issued (diagnostics)
     int pad[2];
     long long cyc[8];       // leader clock64 cycles per phase (diagnostics)
+    long long dbg[16];      // pivot-chain diagnostics (see ldlt_rpm_profile_read)
     int piv_rows[KP_MAX];   // compact rows, pivot order
     uint32_t dval[KP_MAX];  // D diagonal
     uint32_t eval[KP_MAX];  // x at a 2x2 block start, else 0
@@ -82,12 +85,12 @@ struct PanelParams {
     int *idx_next;          // [m]: out, original index of new compact row
     PanelOut *out;
     PanelSync *sync;
-    Event *events;
-    uint32_t *evvec;        // [MAX_EVENTS][EV_WORDS]
+    uint32_t *evlog;        // [MAX_EVENTS][EV_REC] event records
     ScanSlot *scans;        // [MAX_SCANS]
     uint32_t *partner_lp;   // [PARTNER_RING][MAX_PANEL_GRID][KP_MAX]: candidate rows per scan
     int64_t budget_ns;
     int32_t *status;
+    int npend;              // speculative far scans allowed in flight (1..16)
 };
 
 // ---- launchers (host) -------------------------------------------------------

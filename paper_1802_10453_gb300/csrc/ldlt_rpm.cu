@@ -21,11 +21,12 @@
 namespace {
 
 int64_t g_budget_ns = 2000000000LL;
+int g_npend = 16;  // speculative far scans in flight (tunable; LDLT_NPEND)
 
 // ---- profiling (optional) --------------------------------------------------
 struct Prof {
     bool on = false;
-    double acc[16] = {};
+    double acc[32] = {};
     cudaEvent_t evs[2][4] = {};  // two sets: panel i uses set i & 1
     int pending = -1;            // set whose events are recorded but not yet read
     bool ready = false;
@@ -108,7 +109,7 @@ int fp64_kred(uint32_t p)
 struct Layout {
     int64_t ldS;
     size_t S0, S1, Lw, LpT, idx0, idx1, sigma, consumed, piv_all, d_all, e_all, zero_all, zero_cols;
-    size_t out, sync, events, evvec, scans, partner_lp, opA, opB, total;
+    size_t out, sync, evlog, scans, partner_lp, opA, opB, total;
 };
 
 constexpr int MAX_GRID = 1024;
@@ -139,8 +140,7 @@ int make_layout(int64_t n, uint32_t p, int path, Layout &L)
     L.zero_cols = take((size_t)nn * 4);
     L.out = take(sizeof(PanelOut));
     L.sync = take(sizeof(PanelSync));
-    L.events = take((size_t)MAX_EVENTS * sizeof(Event));
-    L.evvec = take((size_t)MAX_EVENTS * EV_WORDS * 4);
+    L.evlog = take((size_t)MAX_EVENTS * EV_REC * 4);
     L.scans = take((size_t)MAX_SCANS * sizeof(ScanSlot));
     L.partner_lp = take((size_t)PARTNER_RING * MAX_PANEL_GRID * KP_MAX * 4);
     if (path == LDLT_PATH_FP64) {
@@ -188,15 +188,22 @@ extern "C" void ldlt_rpm_profile_reset(void)
     g_prof.pending = -1;
 }
 
-extern "C" int ldlt_rpm_profile_read(double out[16])
+extern "C" int ldlt_rpm_profile_read(double out[32])
 {
     if (!out) return LDLT_ERR_ARG;
     prof_collect();
-    for (int i = 0; i < 16; ++i) out[i] = g_prof.acc[i];
+    for (int i = 0; i < 32; ++i) out[i] = g_prof.acc[i];
     return LDLT_OK;
 }
 
 extern "C" void ldlt_rpm_set_wait_budget_ns(int64_t ns) { g_budget_ns = ns > 0 ? ns : 2000000000LL; }
+
+extern "C" int ldlt_rpm_set_speculation(int depth)
+{
+    if (depth < 1 || depth > 16) return LDLT_ERR_ARG;
+    g_npend = depth;
+    return LDLT_OK;
+}
 
 extern "C" int ldlt_rpm_workspace_bytes(int64_t n, uint32_t p, int path, size_t *bytes)
 {
@@ -271,19 +278,21 @@ extern "C" int ldlt_rpm_factor(int64_t n, uint32_t p, uint32_t *A, int64_t lda, 
         pp.LpT = LpT; pp.ldL = ldS;
         pp.consumed = consumed; pp.idx = idxb[cur]; pp.sigma = sigma; pp.idx_next = idxb[cur ^ 1];
         pp.out = out; pp.sync = sync;
-        pp.events = (Event *)(w + Lo.events); pp.evvec = (uint32_t *)(w + Lo.evvec);
+        pp.evlog = (uint32_t *)(w + Lo.evlog);
         pp.scans = (ScanSlot *)(w + Lo.scans); pp.partner_lp = (uint32_t *)(w + Lo.partner_lp);
         pp.budget_ns = g_budget_ns; pp.status = status;
+        pp.npend = g_npend;
         int grid = 1;
         if (m > pp.w) {
-            const int need = 1 + (m - pp.w + ROWS_PER_HELPER - 1) / ROWS_PER_HELPER;
+            // spread the far rows over every SM, at least MIN_HELPER_ROWS rows per helper
+            const int need = 1 + (m - pp.w + MIN_HELPER_ROWS - 1) / MIN_HELPER_ROWS;
             grid = need < nsm ? need : nsm;
             if (grid > MAX_PANEL_GRID) grid = MAX_PANEL_GRID;
         }
         if (prof) CK(cudaEventRecord(ev[0], st));
         CK(launch_panel(pp, grid, st));
         CK(launch_record_panel(out, idxb[cur], r0, z0, piv_all, d_all, e_all, zero_all, zero_cols, st));
-        struct { int h[8]; long long cyc[8]; } rb;
+        struct { int h[8]; long long cyc[8]; long long dbg[16]; } rb;
         static_assert(offsetof(PanelOut, cyc) == 8 * sizeof(int), "PanelOut layout");
         CK(cudaMemcpyAsync(&rb, out, sizeof(rb), cudaMemcpyDeviceToHost, st));
         const int *hdr = rb.h;
@@ -296,6 +305,7 @@ extern "C" int ldlt_rpm_factor(int64_t n, uint32_t p, uint32_t *A, int64_t lda, 
             g_prof.acc[6] += 1;
             g_prof.acc[7] += hdr[5];
             for (int i = 0; i < 8; ++i) g_prof.acc[8 + i] += (double)rb.cyc[i];
+            for (int i = 0; i < 16; ++i) g_prof.acc[16 + i] += (double)rb.dbg[i];
         }
         if (aborted) return LDLT_OK;  // LDLT_ERR_TIMEOUT is in *status
         CK(launch_lw_scatter(LpT, ldS, m, np, idxb[cur], Lw, ldS, r0, st));

@@ -75,6 +75,26 @@ __device__ __forceinline__ int64_t gtime()
     return (int64_t)t;
 }
 
+// Budget check for spin-waits that reads %globaltimer only once every 1024
+// unsuccessful spins (the first read starts the clock), so a wait that is
+// already satisfied costs nothing.
+struct Spin {
+    int64_t t0 = 0;
+    unsigned n = 0;
+    __device__ __forceinline__ bool expired(int64_t budget)
+    {
+        if ((++n & 1023u) != 0) return false;
+        const int64_t t = gtime();
+        if (t0 == 0) { t0 = t; return false; }
+        return t - t0 > budget;
+    }
+};
+
+__device__ __forceinline__ uint32_t pick4(const uint4 &v, int i)
+{
+    return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
+
 // barrier among the 16 compute warps only
 __device__ __forceinline__ void cbar() { asm volatile("bar.sync 1, %0;" ::"n"(NCT) : "memory"); }
 
@@ -96,8 +116,10 @@ constexpr int SRING = 128;                    // posted scan results
 struct Shared {
     uint32_t U[KP_MAX * SSTRIDE];      // U~ columns of this CTA's rows, k-major
     uint32_t ring[NSLOT][EV_WORDS];    // event payloads
+    uint32_t scol[NSLOT][2][SROWS];    // helpers: S(t, a) and S(t, b) of each ring event
+    uint4 sgrp[2][SROWS];              // helpers: S[t][4g .. 4g+3] for two column groups
     Event ev[NSLOT];
-    uint32_t za[KP_MAX], zb[KP_MAX], ub[KP_MAX];
+    uint32_t ub[KP_MAX];               // U~ row of a 2x2 partner
     uint8_t kind[KP_MAX];              // column kinds of this panel
     uint32_t bw[KP_MAX];               // w_B, at the block's first column
     uint32_t mx[KP_MAX], my[KP_MAX];   // x~, y~ of a 2x2 block (first column)
@@ -116,7 +138,8 @@ struct Shared {
     // the panel back to that row.
     int pend_id[NPEND], pend_row[NPEND], pend_np[NPEND], pend_nz[NPEND];
     uint32_t pend_W[NPEND];
-    uint32_t pend_bw[NPEND][KP_MAX];
+    uint32_t pend_bw[NPEND][KP_MAX];   // w_B when the scan was issued
+    uint32_t delta[KP_MAX];            // delta_B at the block's first column
     int res_min[SRING];
     int redi[32];
     uint32_t xy[4];
@@ -124,14 +147,14 @@ struct Shared {
     volatile int ev_ready;             // events written to the ring (leader) / fetched (helper)
     volatile int ev_done;              // events published (leader) / processed (helper)
     volatile int quit;
+    volatile int ev_fetched;           // helpers: event records fetched (poller -> column loader)
     volatile int nscan_pub;            // scans published (leader -> watcher warp)
     volatile int scan_resolved;        // scans answered by every helper (watcher -> leader)
     uint32_t W;
     int np, ia, nzero, nscan, abort, b, owner, nblk;
-    int ph, pt;                        // pending scans [ph, pt)
-    int rb, rb_b;                      // rollback request
-    int force_b, force_sid;            // partner found by a resolved scan
+    int ph_new, rb, rb_b;              // posted by thread 0: pending head, rollback request
     int nrollback;
+    long long dbg[16];                 // diagnostics (thread-0 / lane-0 owned slots)
 };
 
 __device__ void raise_timeout(const PanelParams &P)
@@ -155,9 +178,9 @@ __device__ __forceinline__ uint32_t zval(int k, const uint32_t *u, int stride, c
 // = tid & 1 takes every other k).  All 32 lanes must call it (pair shuffle);
 // invalid rows compute nothing and return 0.
 template <bool BIG>
-__device__ __forceinline__ uint32_t schur2(const PanelParams &P, const uint32_t *sU, int lrow, int grow, int a,
-                                          uint32_t W, const uint32_t *z, int np, int half, bool valid,
-                                          bool in_smem)
+__device__ __forceinline__ uint32_t schur2(const PanelParams &P, const uint32_t *sU, int lrow, int grow,
+                                          uint32_t sval, uint32_t W, const uint32_t *z, int np, int half,
+                                          bool valid, bool in_smem)
 {
     uint64_t acc = 0;
     if (valid) {
@@ -173,7 +196,7 @@ __device__ __forceinline__ uint32_t schur2(const PanelParams &P, const uint32_t 
     const uint32_t part = fp_reduce64(acc, P.f);
     const uint32_t other = __shfl_xor_sync(0xffffffffu, part, 1);
     if (!valid) return 0u;
-    return fp_sub(fp_mul(W, s_at(P.S, P.ldS, grow, a), P.f), fp_add(part, other, P.f), P.f);
+    return fp_sub(fp_mul(W, sval, P.f), fp_add(part, other, P.f), P.f);
 }
 
 // Rewrite the U~ values of one row as true L values (in global memory), using
@@ -204,7 +227,7 @@ __device__ void helper_cta(const PanelParams &P, Shared &sh, int lo, int hi)
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     const int nrows = hi > lo ? hi - lo : 0;
-    if (tid == 0) { sh.ev_ready = 0; sh.ev_done = 0; sh.quit = 0; }
+    if (tid == 0) { sh.ev_ready = 0; sh.ev_done = 0; sh.quit = 0; sh.ev_fetched = 0; }
     __syncthreads();
 
     if (warp == NCW) {
@@ -213,7 +236,7 @@ __device__ void helper_cta(const PanelParams &P, Shared &sh, int lo, int hi)
         for (;;) {
             int avail = 0;
             if (lane == 0) {
-                const int64_t t0 = gtime();
+                Spin sp;
                 volatile int *cnt = &P.sync->ev_count;
                 volatile int *ab = &P.sync->abort;
                 for (;;) {
@@ -222,7 +245,7 @@ __device__ void helper_cta(const PanelParams &P, Shared &sh, int lo, int hi)
                     const int lim = c < room ? c : room;
                     if (lim > e) { avail = lim - e; break; }
                     if (*ab) break;
-                    if (gtime() - t0 > P.budget_ns) { raise_timeout(P); break; }
+                    if (sp.expired(P.budget_ns)) { raise_timeout(P); break; }
                 }
             }
             avail = __shfl_sync(0xffffffffu, avail, 0);
@@ -233,40 +256,125 @@ __device__ void helper_cta(const PanelParams &P, Shared &sh, int lo, int hi)
             __threadfence();
             bool end = false;
             for (int q = 0; q < avail; ++q) {
+                // one round trip: header and the first 2*KP_MAX payload words
                 const int ee = e + q, s = ee % NSLOT;
-                const int *gh = reinterpret_cast<const int *>(&P.events[ee]);
-                const int hv = lane < 8 ? __ldcg(gh + lane) : 0;
-                const int kind = __shfl_sync(0xffffffffu, hv, 0);
-                const int np = __shfl_sync(0xffffffffu, hv, 3);
-                if (lane < 8) reinterpret_cast<int *>(&sh.ev[s])[lane] = hv;
-                const uint32_t *vv = P.evvec + (int64_t)ee * EV_WORDS;
-                const int words = (kind == EV_END) ? 3 * KP_MAX : (kind == EV_PIVOT2 ? 2 * KP_MAX : KP_MAX);
-                for (int k = lane; k < words; k += 32) {
-                    const int kk = k % KP_MAX;
-                    if (kind == EV_END || kk < np) sh.ring[s][k] = __ldcg(vv + k);
+                const uint4 *rec = reinterpret_cast<const uint4 *>(P.evlog + (int64_t)ee * EV_REC);
+                constexpr int NCH = (8 + 2 * KP_MAX) / 4;
+                uint4 c0 = __ldcg(rec + lane), c1 = __ldcg(rec + lane + 32), c2 = make_uint4(0, 0, 0, 0);
+                if (lane + 64 < NCH) c2 = __ldcg(rec + lane + 64);
+                uint4 *ringv = reinterpret_cast<uint4 *>(sh.ring[s]);
+                uint4 *evv = reinterpret_cast<uint4 *>(&sh.ev[s]);
+                if (lane < 2) evv[lane] = c0; else ringv[lane - 2] = c0;
+                ringv[lane + 30] = c1;
+                if (lane + 64 < NCH) ringv[lane + 62] = c2;
+                const int kind = __shfl_sync(0xffffffffu, (int)c0.x, 0);
+                if (kind == EV_END) {
+                    // the end record carries 3*KP_MAX payload words
+                    for (int k = 2 * KP_MAX / 4 + lane; k < 3 * KP_MAX / 4; k += 32)
+                        ringv[k] = __ldcg(rec + 2 + k);
+                    end = true;
                 }
-                end = end || (kind == EV_END);
             }
             __threadfence_block();
             __syncwarp();
-            if (lane == 0) sh.ev_ready = e + avail;
+            if (lane == 0) sh.ev_fetched = e + avail;
             if (end) return;
             e += avail;
         }
     }
-    if (warp > NCW) return;  // the second service warp has no work in a helper
-
+    if (warp == NCW + 1) {
+        // ---- column loader: S(t, a) (and S(t, b)) of each fetched event for this CTA's rows ----
+        // Columns come in groups of four (16-byte rows of S) kept in shared
+        // memory; the next group is fetched with cp.async while the current
+        // one serves events, so most events cost a shared-memory copy.
+        const int nr = nrows < SROWS ? nrows : SROWS;
+        int gbuf_g[2] = {-1, -1};
+        int last_g = -1;  // group of the most recent cp.async commit
+        auto fetch_grp = [&](int g, int bi) {
+            for (int lr = lane; lr < nr; lr += 32) {
+                const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&sh.sgrp[bi][lr]);
+                const uint32_t *src = P.S + (int64_t)(lo + lr) * P.ldS + 4 * g;
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            gbuf_g[bi] = g;
+        };
+        for (int e = 0;; ++e) {
+            int go = 0;
+            if (lane == 0) {
+                Spin sp;
+                for (;;) {
+                    if (sh.ev_fetched > e) { go = 1; break; }
+                    if (sh.quit) break;
+                    __nanosleep(16);
+                    if (sp.expired(2 * P.budget_ns + 1000000)) break;
+                }
+            }
+            go = __shfl_sync(0xffffffffu, go, 0);
+            if (!go) break;
+            __threadfence_block();
+            const int s = e % NSLOT;
+            const int kind = sh.ev[s].kind, ea = sh.ev[s].a, eb = sh.ev[s].b;
+            if (kind == EV_PIVOT1 || kind == EV_PIVOT2 || kind == EV_SCAN) {
+                const int g = ea >> 2;
+                int bi = (gbuf_g[0] == g) ? 0 : ((gbuf_g[1] == g) ? 1 : -1);
+                if (bi < 0) {
+                    // not resident (first event, or the row index went back): fetch now
+                    asm volatile("cp.async.wait_group 0;" ::: "memory");
+                    __syncwarp();
+                    bi = (gbuf_g[0] == g + 1) ? 1 : 0;
+                    fetch_grp(g, bi);
+                    last_g = g;
+                }
+                // group g was committed before a later prefetch unless it is the last commit
+                if (last_g == g) asm volatile("cp.async.wait_group 0;" ::: "memory");
+                else asm volatile("cp.async.wait_group 1;" ::: "memory");
+                __syncwarp();
+                // t > a for every far row t: column a of row t
+                const int c = ea & 3;
+                for (int lr = lane; lr < nr; lr += 32) sh.scol[s][0][lr] = pick4(sh.sgrp[bi][lr], c);
+                if (kind == EV_PIVOT2)
+                    for (int lr = lane; lr < nr; lr += 32) sh.scol[s][1][lr] = s_at(P.S, P.ldS, lo + lr, eb);
+                __syncwarp();
+                if (gbuf_g[bi ^ 1] != g + 1) {
+                    // prefetch the next group into the other buffer once nothing is in flight
+                    if (last_g != g) asm volatile("cp.async.wait_group 0;" ::: "memory");
+                    __syncwarp();
+                    fetch_grp(g + 1, bi ^ 1);
+                    last_g = g + 1;
+                }
+            }
+            __threadfence_block();
+            __syncwarp();
+            if (lane == 0) sh.ev_ready = e + 1;
+            if (kind == EV_END) break;
+        }
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        return;
+    }
     // ---- compute warps ----
     const int half = tid & 1;
+    long long hidle = 0, hbusy = 0, hmark = clock64();
+    auto hflush = [&]() {
+        if (tid == 0 && blockIdx.x == 1) {
+            P.out->dbg[5] = hidle; P.out->dbg[6] = hbusy;
+        }
+    };
     for (int e = 0;; ++e) {
         if (tid == 0) {
-            const int64_t t0 = gtime();
+            const long long tw = clock64();
+            hbusy += tw - hmark;
+            Spin sp;
             while (sh.ev_ready <= e && !sh.quit) {
-                if (gtime() - t0 > 2 * P.budget_ns + 1000000) break;
+                __nanosleep(32);
+                if (sp.expired(2 * P.budget_ns + 1000000)) break;
             }
+            hmark = clock64();
+            hidle += hmark - tw;
+            if (blockIdx.x == 1) P.out->dbg[7] = e;
         }
         cbar();
-        if (sh.ev_ready <= e) return;  // quit or abort
+        if (sh.ev_ready <= e) { hflush(); return; }  // quit or abort
         __threadfence_block();
         const int s = e % NSLOT;
         const int kind = sh.ev[s].kind;
@@ -286,6 +394,7 @@ __device__ void helper_cta(const PanelParams &P, Shared &sh, int lo, int hi)
                 if (lr < SROWS) finish_row(P, sh.U + lr, SSTRIDE, P.LpT + t, np, sh.kind, cA, cB);
                 else finish_row(P, P.LpT + t, (int)P.ldL, P.LpT + t, np, sh.kind, cA, cB);
             }
+            hflush();
             return;
         }
         int firstnz = INT_MAX;
@@ -294,22 +403,24 @@ __device__ void helper_cta(const PanelParams &P, Shared &sh, int lo, int hi)
             const bool valid = lr < nrows;
             const bool sm = lr < SROWS;
             const int t = lo + lr;
+            const uint32_t sa = valid ? (sm ? sh.scol[s][0][lr] : s_at(P.S, P.ldS, t, a)) : 0u;
             if (kind == EV_PIVOT1) {
-                const uint32_t c = schur2<BIG>(P, sh.U, lr, t, a, W, za, np, half, valid, sm);
+                const uint32_t c = schur2<BIG>(P, sh.U, lr, t, sa, W, za, np, half, valid, sm);
                 if (valid && half == 0) {
                     if (sm) sh.U[np * SSTRIDE + lr] = c;
                     P.LpT[(int64_t)np * P.ldL + t] = c;
                 }
             } else if (kind == EV_PIVOT2) {
-                const uint32_t ca = schur2<BIG>(P, sh.U, lr, t, a, W, za, np, half, valid, sm);
-                const uint32_t cb = schur2<BIG>(P, sh.U, lr, t, b, W, zb, np, half, valid, sm);
+                const uint32_t sb = valid ? (sm ? sh.scol[s][1][lr] : s_at(P.S, P.ldS, t, b)) : 0u;
+                const uint32_t ca = schur2<BIG>(P, sh.U, lr, t, sa, W, za, np, half, valid, sm);
+                const uint32_t cb = schur2<BIG>(P, sh.U, lr, t, sb, W, zb, np, half, valid, sm);
                 if (valid && half == 0) {
                     if (sm) { sh.U[np * SSTRIDE + lr] = ca; sh.U[(np + 1) * SSTRIDE + lr] = cb; }
                     P.LpT[(int64_t)np * P.ldL + t] = ca;
                     P.LpT[(int64_t)(np + 1) * P.ldL + t] = cb;
                 }
             } else {  // EV_SCAN
-                const uint32_t c = schur2<BIG>(P, sh.U, lr, t, a, W, za, np, half, valid, sm);
+                const uint32_t c = schur2<BIG>(P, sh.U, lr, t, sa, W, za, np, half, valid, sm);
                 if (valid && c != 0 && t < firstnz) firstnz = t;
             }
         }
@@ -321,18 +432,21 @@ __device__ void helper_cta(const PanelParams &P, Shared &sh, int lo, int hi)
             for (int i = 0; i < NCW; ++i) mn = min(mn, sh.redi[i]);
             const int sid = sh.ev[s].scan_id;
             if (mn != INT_MAX) {
+                // a hit: publish the candidate's columns, then the row index, then the count
                 const int lr = mn - lo;
                 uint32_t *dst = P.partner_lp +
                                 ((int64_t)(sid % PARTNER_RING) * MAX_PANEL_GRID + blockIdx.x) * KP_MAX;
                 for (int k = tid; k < np; k += NCT)
                     dst[k] = lr < SROWS ? sh.U[k * SSTRIDE + lr] : P.LpT[(int64_t)k * P.ldL + mn];
-            }
-            __threadfence();
-            cbar();
-            if (tid == 0) {
-                if (mn != INT_MAX) atomicMin(&P.scans[sid].min, mn);
                 __threadfence();
-                atomicAdd(&P.scans[sid].done, 1);
+                cbar();
+                if (tid == 0) {
+                    atomicMin(&P.scans[sid].min, mn);
+                    __threadfence();
+                    atomicAdd(&P.scans[sid].done, 1);
+                }
+            } else if (tid == 0) {
+                atomicAdd(&P.scans[sid].done, 1);  // a miss: nothing to order before the count
             }
         }
         cbar();
@@ -355,8 +469,9 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
     if (tid == 0) {
         sh.np = 0; sh.ia = 0; sh.nzero = 0; sh.nscan = 0; sh.abort = 0; sh.nblk = 0;
         sh.ev_ready = 0; sh.ev_done = 0; sh.quit = 0; sh.W = 1u;
-        sh.nscan_pub = 0; sh.scan_resolved = 0; sh.ph = 0; sh.pt = 0;
-        sh.rb = -1; sh.force_b = -1; sh.force_sid = -1; sh.nrollback = 0;
+        sh.nscan_pub = 0; sh.scan_resolved = 0; sh.ph_new = 0;
+        sh.rb = -1; sh.nrollback = 0;
+        for (int i = 0; i < 16; ++i) sh.dbg[i] = 0;
     }
     __syncthreads();
 
@@ -368,12 +483,13 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
         for (;;) {
             int ready = 0;
             if (lane == 0) {
-                const int64_t t0 = gtime();
+                Spin sp;
                 for (;;) {
                     const int r = sh.ev_ready;
                     if (r > e) { ready = r; break; }
                     if (sh.quit) break;
-                    if (gtime() - t0 > 4 * P.budget_ns + 1000000) break;
+                    __nanosleep(20);
+                    if (sp.expired(4 * P.budget_ns + 1000000)) break;
                 }
             }
             ready = __shfl_sync(0xffffffffu, ready, 0);
@@ -383,14 +499,13 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
             for (int ee = e; ee < ready; ++ee) {
                 const int s = ee % NSLOT;
                 const int kind = sh.ev[s].kind, np = sh.ev[s].np;
-                uint32_t *vv = P.evvec + (int64_t)ee * EV_WORDS;
+                uint32_t *rec = P.evlog + (int64_t)ee * EV_REC;
                 const int words = (kind == EV_END) ? 3 * KP_MAX : (kind == EV_PIVOT2 ? 2 * KP_MAX : KP_MAX);
                 for (int k = lane; k < words; k += 32) {
                     const int kk = k % KP_MAX;
-                    if (kind == EV_END || kk < np) vv[k] = sh.ring[s][k];
+                    if (kind == EV_END || kk < np) rec[8 + k] = sh.ring[s][k];
                 }
-                if (lane < 8)
-                    reinterpret_cast<int *>(&P.events[ee])[lane] = reinterpret_cast<const int *>(&sh.ev[s])[lane];
+                if (lane < 8) rec[lane] = reinterpret_cast<const uint32_t *>(&sh.ev[s])[lane];
                 if (kind == EV_SCAN && lane == 0) {
                     P.scans[sh.ev[s].scan_id].done = 0;
                     P.scans[sh.ev[s].scan_id].min = INT_MAX;
@@ -402,6 +517,8 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
             __syncwarp();
             if (lane == 0) {
                 atomicExch(&P.sync->ev_count, ready);
+                sh.dbg[8] += 1;
+                sh.dbg[9] += ready - e;
                 sh.ev_done = ready;
                 if (last_scan >= 0) sh.nscan_pub = last_scan + 1;  // the watcher may poll those slots now
             }
@@ -416,21 +533,22 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
         for (int id = 0;; ++id) {
             int go = 0, v = INT_MAX;
             if (lane == 0) {
-                int64_t t0 = gtime();
+                Spin sp;
                 for (;;) {
                     if (sh.nscan_pub > id) { go = 1; break; }
                     if (sh.quit) break;
-                    if (gtime() - t0 > 4 * P.budget_ns + 1000000) break;
+                    __nanosleep(32);
+                    if (sp.expired(4 * P.budget_ns + 1000000)) break;
                 }
                 if (go) {
                     go = 0;
                     volatile int *done = &P.scans[id].done;
                     volatile int *ab = &P.sync->abort;
-                    t0 = gtime();
+                    Spin sp2;
                     for (;;) {
                         if (*done >= nh) { go = 1; break; }
                         if (*ab || sh.quit) break;
-                        if (gtime() - t0 > P.budget_ns) { raise_timeout(P); break; }
+                        if (sp2.expired(P.budget_ns)) { raise_timeout(P); break; }
                     }
                     if (go) {
                         __threadfence();
@@ -447,143 +565,199 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
     }
 
     // ---- compute warps: 512 threads, two per window row ----
+    // The control state lives in registers, identical in every compute
+    // thread: each update is computed from values every thread reads after
+    // a barrier, so the threads never diverge on it.
     const int half = tid & 1;
     const int lr = tid >> 1;  // window row of this thread pair
     const bool inwin = lr < w;
+    int np = 0, ia = 0, nzero = 0, nscan = 0, ph = 0, pt = 0, ev_next = 0, nrb = 0;
+    int force_b = -1, force_sid = -1;
+    uint32_t W = 1u;
+    // S[lr][4g .. 4g+3] of this thread's window row for the current column
+    // group g = a / 4 and the next one: one 16-byte load per four rows, issued
+    // a group ahead, keeps the DRAM latency off the per-row chain
+    uint4 g_cur = make_uint4(0, 0, 0, 0), g_nxt = make_uint4(0, 0, 0, 0);
+    int cur_g = -1, nxt_g = -1;
+    auto load_grp = [&](int g) -> uint4 {
+        if (inwin && lr >= 4 * g) return __ldg(reinterpret_cast<const uint4 *>(P.S + (int64_t)lr * P.ldS + 4 * g));
+        return make_uint4(0, 0, 0, 0);
+    };
 
-    // Put an event in the ring.  Called by warp 0 only (all its lanes): the
-    // other warps go on, and the payload vectors are not rewritten before the
-    // next compute barrier.
-    auto push_w0 = [&](int kind, int a, int b, int np, uint32_t s0, int scan_id, const uint32_t *p0,
-                       const uint32_t *p1, const uint32_t *p2, int nwords) {
-        const int e = sh.ev_ready;
-        if (lane == 0) {
-            const int64_t t0 = gtime();
+    // ring slot e % NSLOT may be written once event e - NSLOT is published
+    auto ring_ready = [&](int e) {
+        if (sh.ev_done <= e - NSLOT) {
+            Spin sp;
             while (sh.ev_done <= e - NSLOT) {
-                if (gtime() - t0 > P.budget_ns) { raise_timeout(P); sh.abort = 1; break; }
+                __nanosleep(16);
+                if (sp.expired(P.budget_ns)) { raise_timeout(P); sh.abort = 1; break; }
             }
         }
-        __syncwarp();
-        const int s = e % NSLOT;
-        for (int k = lane; k < nwords; k += 32) {
-            sh.ring[s][k] = p0[k];
-            if (p1) sh.ring[s][KP_MAX + k] = p1[k];
-            if (p2) sh.ring[s][2 * KP_MAX + k] = p2[k];
-        }
-        if (lane == 0) {
-            sh.ev[s].kind = kind; sh.ev[s].a = a; sh.ev[s].b = b; sh.ev[s].np = np;
-            sh.ev[s].s0 = s0; sh.ev[s].s1 = 0; sh.ev[s].scan_id = scan_id; sh.ev[s].pad = 0;
-        }
-        __syncwarp();
-        if (lane == 0) { __threadfence_block(); sh.ev_ready = e + 1; }
-        __syncwarp();
     };
-    // Thread 0: take in answered scans, oldest first; a hit asks for a rollback.
-    auto check_scans = [&]() {
-        sh.rb = -1;
-        while (sh.ph < sh.pt) {
-            const int k = sh.ph;
-            const int id = sh.pend_id[k % NPEND];
-            if (sh.scan_resolved <= id) break;
-            const int v = sh.res_min[id % SRING];
-            if (v >= w && v < P.m) { sh.rb = k; sh.rb_b = v; break; }
-            sh.ph = k + 1;  // confirmed: that row is a zero row
-        }
-    };
-    // Thread 0: wait until the oldest pending scan is answered.
-    auto wait_head = [&]() {
-        const int id = sh.pend_id[sh.ph % NPEND];
-        const int64_t t0 = gtime();
-        while (sh.scan_resolved <= id) {
-            if (gtime() - t0 > P.budget_ns) { raise_timeout(P); sh.abort = 1; break; }
+    // thread 0: take in answered scans, oldest first; posts the new head and
+    // a rollback request (index of the scan that found a partner, or -1)
+    auto check_scans = [&](bool wait_oldest) {
+        if (wait_oldest && ph < pt) {
+            const int id = sh.pend_id[ph % NPEND];
+            Spin sp;
+            while (sh.scan_resolved <= id) {
+                __nanosleep(16);
+                if (sp.expired(P.budget_ns)) { raise_timeout(P); sh.abort = 1; break; }
+            }
+            sh.dbg[1] += 1;
         }
         __threadfence_block();
+        int q = ph, rb = -1, rb_b = 0;
+        while (q < pt) {
+            const int id = sh.pend_id[q % NPEND];
+            if (sh.scan_resolved <= id) break;
+            const int v = sh.res_min[id % SRING];
+            if (v >= w && v < P.m) { rb = q; rb_b = v; break; }
+            ++q;  // confirmed: that row is a zero row
+        }
+        sh.ph_new = q;
+        sh.rb = rb;
+        sh.rb_b = rb_b;
+    };
+    // all compute threads: roll back to pending scan k, which found partner b
+    auto rollback = [&](int k, int bfound) {
+        const int slot = k % NPEND;
+        const int ak = sh.pend_row[slot], npk = sh.pend_np[slot];
+        for (int j = npk + tid; j < np; j += NCT)
+            if (sh.kind[j] == K_2B) P.consumed[sh.piv_rows[j]] = 0;
+        for (int t = ak + tid; t < w; t += NCT) sh.wstate[t] = 0;
+        cbar();
+        for (int j = tid; j < npk; j += NCT) {
+            if (sh.kind[j] == K_2B) {
+                const int bb = sh.piv_rows[j];
+                if (bb >= ak && bb < w) sh.wstate[bb] = 1;
+            }
+            sh.bw[j] = sh.pend_bw[slot][j];
+        }
+        for (int q = tid; q < (np - npk) * w; q += NCT) {
+            const int j = npk + q / w, t = q % w;
+            sh.U[j * SSTRIDE + t] = 0;
+            P.LpT[(int64_t)j * P.ldL + t] = 0;
+        }
+        np = npk;
+        nzero = sh.pend_nz[slot];
+        ia = ak;
+        W = sh.pend_W[slot];
+        force_b = bfound;
+        force_sid = sh.pend_id[slot];
+        pt = k;  // this and every later pending scan are dropped (ph == k)
+        ++nrb;
+        cbar();
     };
 
     long long cyc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     long long tmark = clock64();
-    auto lap = [&](int ph) {
-        if (tid == 0) { const long long t = clock64(); cyc[ph] += t - tmark; tmark = t; }
+    auto lap = [&](int phz) {
+        if (tid == 0) { const long long t = clock64(); cyc[phz] += t - tmark; tmark = t; }
     };
 
     for (;;) {
-        if (sh.rb >= 0) {
-            // ---- roll back to the row whose scan found a partner ----
-            const int slot = sh.rb % NPEND;
-            const int ak = sh.pend_row[slot], npk = sh.pend_np[slot];
-            const int np_cur = sh.np;
-            for (int j = tid; j < np_cur; j += NCT)
-                if (j >= npk && sh.kind[j] == K_2B) P.consumed[sh.piv_rows[j]] = 0;
-            for (int t = ak + tid; t < w; t += NCT) sh.wstate[t] = 0;
-            cbar();
-            for (int j = tid; j < npk; j += NCT)
-                if (sh.kind[j] == K_2B) {
-                    const int bb = sh.piv_rows[j];
-                    if (bb >= ak && bb < w) sh.wstate[bb] = 1;
-                }
-            for (int q = tid; q < (np_cur - npk) * w; q += NCT) {
-                const int j = npk + q / w, t = q % w;
-                sh.U[j * SSTRIDE + t] = 0;
-                P.LpT[(int64_t)j * P.ldL + t] = 0;
-            }
-            for (int k = tid; k < npk; k += NCT) sh.bw[k] = sh.pend_bw[slot][k];
-            if (tid == 0) {
-                sh.np = npk; sh.nzero = sh.pend_nz[slot]; sh.ia = ak; sh.W = sh.pend_W[slot];
-                sh.force_b = sh.rb_b; sh.force_sid = sh.pend_id[slot];
-                sh.pt = sh.rb;  // drop this and every later pending scan
-                sh.nrollback += 1;
-                sh.rb = -1;
-            }
-            cbar();
-            lap(1);
-            continue;
-        }
-        const int np = sh.np, ia = sh.ia;
-        if (sh.abort) break;
-        const bool full = np > P.kp - 2 || ia >= w || sh.ev_ready > MAX_EVENTS - 64 || sh.nscan > MAX_SCANS - 64;
+        const bool full = np > P.kp - 2 || ia >= w || ev_next > MAX_EVENTS - 64 || nscan > MAX_SCANS - 64;
         if (full) {
-            if (sh.ph == sh.pt) break;  // nothing in flight: the panel is complete
-            if (tid == 0) { wait_head(); check_scans(); }
+            if (ph == pt) break;  // nothing in flight: the panel is complete
+            if (tid == 0) check_scans(true);
             cbar();
+            ph = sh.ph_new;
+            const int rb = sh.rb, rb_b = sh.rb_b;
+            const bool ab = sh.abort;
+            cbar();
+            if (ab) break;
+            if (rb >= 0) rollback(rb, rb_b);
+            lap(6);
             continue;
         }
         if (sh.wstate[ia]) {
-            if (tid == 0) { sh.ia = ia + 1; check_scans(); }
-            cbar();
+            ++ia;
             continue;
         }
         const int a = ia;
-        const uint32_t W = sh.W;
-        for (int k = tid; k < np; k += NCT) sh.za[k] = zval(k, sh.U + a, SSTRIDE, sh, f);
+        const int slot = ev_next % NSLOT;
+        uint32_t *za = sh.ring[slot];
+        uint32_t *zb = sh.ring[slot] + KP_MAX;
+        if (tid < np) {
+            ring_ready(ev_next);
+            za[tid] = zval(tid, sh.U + a, SSTRIDE, sh, f);
+            sh.pend_bw[pt % NPEND][tid] = sh.bw[tid];  // kept only if this row's scan is issued
+        }
+        if (tid == 0) {
+            sh.dbg[0] += 1;
+            check_scans(false);
+        }
+        const bool myrow = inwin && lr >= a;
+        {
+            const int g = a >> 2;
+            if (g != cur_g) {
+                g_cur = (nxt_g == g) ? g_nxt : load_grp(g);
+                cur_g = g;
+                if (4 * (g + 1) < w) g_nxt = load_grp(g + 1);
+                nxt_g = g + 1;
+            }
+        }
+        const uint32_t s_col = myrow ? pick4(g_cur, a & 3) : 0u;
+        const long long tb1 = clock64();
         cbar();
+        const long long ta1 = clock64();
+        {
+            ph = sh.ph_new;
+            const int rb = sh.rb, rb_b = sh.rb_b;
+            if (sh.abort) break;
+            if (rb >= 0) {
+                cbar();  // every thread has read the posted request
+                rollback(rb, rb_b);
+                lap(5);
+                continue;
+            }
+        }
+        lap(0);
         // c~_a[t] for the window rows t >= a (t = a included) and the first
         // non-zero of row a beyond a inside the window, in one pass
-        const uint32_t ca_t = schur2<BIG>(P, sh.U, lr, lr, a, W, sh.za, np, half, inwin && lr >= a, true);
+        const uint32_t ca_t = schur2<BIG>(P, sh.U, lr, lr, s_col, W, za, np, half, myrow, true);
         if (lr == a && half == 0) sh.caa = ca_t;
         int firstnz = (half == 0 && inwin && lr > a && ca_t != 0) ? lr : INT_MAX;
         for (int o = 16; o > 0; o >>= 1) firstnz = min(firstnz, __shfl_xor_sync(0xffffffffu, firstnz, o));
         if (lane == 0) sh.redi[warp] = firstnz;
+        const long long tb2 = clock64();
         cbar();
-        lap(0);
+        const long long ta2 = clock64();
+        if (tid == 0 || tid == NCT - 1) {
+            const int o = (tid == 0) ? 10 : 12;
+            sh.dbg[o] += ta1 - tb1;       // wait at barrier 1
+            sh.dbg[o + 1] += ta2 - tb2;   // wait at barrier 2
+            if (tid == 0) sh.dbg[14] += tb2 - ta1;  // schur phase (thread 0)
+            else sh.dbg[15] += tb2 - ta1;
+        }
+        lap(1);
         const uint32_t caa = sh.caa;
 
         if (caa != 0) {
             // ---- 1x1 pivot: U~[:, np] = c~_a, delta = W c~_a[a] ----
-            if (inwin && lr >= a && half == 0) {
+            if (myrow && half == 0) {
                 sh.U[np * SSTRIDE + lr] = ca_t;
                 P.LpT[(int64_t)np * P.ldL + lr] = ca_t;
             }
             const uint32_t delta = fp_mul(W, caa, f);
-            for (int k = tid; k < np; k += NCT)
-                if (sh.kind[k] != K_2B) sh.bw[k] = fp_mul(sh.bw[k], delta, f);
-            if (helpers && warp == 0) push_w0(EV_PIVOT1, a, -1, np, W, 0, sh.za, nullptr, nullptr, np);
+            if (tid < np && sh.kind[tid] != K_2B) sh.bw[tid] = fp_mul(sh.bw[tid], delta, f);
             if (tid == 0) {
-                sh.kind[np] = K_1x1; sh.bw[np] = W; sh.piv[np] = caa; sh.w0[np] = W;
-                sh.W = fp_mul(W, delta, f);
+                if (helpers) {
+                    Event &ev = sh.ev[slot];
+                    ev.kind = EV_PIVOT1; ev.a = a; ev.b = -1; ev.np = np; ev.s0 = W; ev.s1 = 0;
+                    ev.scan_id = 0; ev.pad = 0;
+                    __threadfence_block();
+                    sh.ev_ready = ev_next + 1;
+                }
+                sh.kind[np] = K_1x1; sh.bw[np] = W; sh.piv[np] = caa; sh.w0[np] = W; sh.delta[np] = delta;
                 sh.piv_rows[np] = a;
-                sh.wstate[a] = 1; sh.np = np + 1; sh.ia = ia + 1;
-                check_scans();
+                sh.wstate[a] = 1;
             }
+            W = fp_mul(W, delta, f);
+            ++np;
+            ++ia;
+            if (helpers) ++ev_next;
             cbar();
             lap(2);
             continue;
@@ -591,69 +765,74 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
 
         int b = INT_MAX;
         bool far = false;
-        if (sh.force_b >= 0) {
+        if (force_b >= 0) {
             // partner found by this row's scan before the rollback
-            b = sh.force_b;
+            b = force_b;
             far = true;
             const int chunk = (P.m - w + nh - 1) / nh;
             const int owner = 1 + (b - w) / chunk;
             const uint32_t *src = P.partner_lp +
-                                  ((int64_t)(sh.force_sid % PARTNER_RING) * MAX_PANEL_GRID + owner) * KP_MAX;
-            for (int k = tid; k < np; k += NCT) sh.ub[k] = __ldcg(src + k);
+                                  ((int64_t)(force_sid % PARTNER_RING) * MAX_PANEL_GRID + owner) * KP_MAX;
+            if (tid < np) sh.ub[tid] = __ldcg(src + tid);
         } else {
             for (int i = 0; i < NCW; ++i) b = min(b, sh.redi[i]);
         }
-        lap(3);
         if (b == INT_MAX && helpers) {
             // ---- speculative far scan: publish it and go on as if the row were zero ----
-            if (sh.pt - sh.ph >= NPEND) {
-                if (tid == 0) { wait_head(); check_scans(); }
+            if (pt - ph >= P.npend) {
+                if (tid == 0) check_scans(true);
                 cbar();
+                ph = sh.ph_new;
+                const int rb = sh.rb, rb_b = sh.rb_b;
+                const bool ab = sh.abort;
+                cbar();
+                if (ab) break;
+                if (rb >= 0) rollback(rb, rb_b);
+                lap(6);
                 continue;  // the row is taken again from the top
             }
-            const int sid = sh.nscan;
-            const int slot = sh.pt % NPEND;
-            if (warp == 0) {
-                push_w0(EV_SCAN, a, -1, np, W, sid, sh.za, nullptr, nullptr, np);
-                for (int k = lane; k < np; k += 32) sh.pend_bw[slot][k] = sh.bw[k];
-            }
             if (tid == 0) {
-                sh.pend_id[slot] = sid; sh.pend_row[slot] = a; sh.pend_np[slot] = np;
-                sh.pend_nz[slot] = sh.nzero; sh.pend_W[slot] = W;
-                sh.pt = sh.pt + 1;
-                sh.nscan = sid + 1;
-                sh.zero_rows[sh.nzero] = a; sh.zero_np[sh.nzero] = np; sh.nzero += 1;
-                sh.wstate[a] = 1; sh.ia = ia + 1;
-                check_scans();
+                Event &ev = sh.ev[slot];
+                ev.kind = EV_SCAN; ev.a = a; ev.b = -1; ev.np = np; ev.s0 = W; ev.s1 = 0;
+                ev.scan_id = nscan; ev.pad = 0;
+                const int ps = pt % NPEND;
+                sh.pend_id[ps] = nscan; sh.pend_row[ps] = a; sh.pend_np[ps] = np;
+                sh.pend_nz[ps] = nzero; sh.pend_W[ps] = W;
+                sh.zero_rows[nzero] = a; sh.zero_np[nzero] = np;
+                sh.wstate[a] = 1;
+                __threadfence_block();
+                sh.ev_ready = ev_next + 1;
             }
-            cbar();
-            lap(4);
+            ++nscan;
+            ++pt;
+            ++nzero;
+            ++ia;
+            ++ev_next;
+            lap(3);
             continue;
         }
         if (b == INT_MAX) {
             // ---- zero row (no far rows to search) ----
             if (tid == 0) {
-                sh.zero_rows[sh.nzero] = a; sh.zero_np[sh.nzero] = np; sh.nzero += 1;
-                sh.wstate[a] = 1; sh.ia = ia + 1;
+                sh.zero_rows[nzero] = a; sh.zero_np[nzero] = np;
+                sh.wstate[a] = 1;
             }
-            cbar();
-            lap(6);
+            ++nzero;
+            ++ia;
             continue;
         }
 
         // ---- 2x2 pivot on (a, b) ----
-        if (!far)
-            for (int k = tid; k < np; k += NCT) sh.ub[k] = sh.U[k * SSTRIDE + b];
+        if (!far && tid < np) sh.ub[tid] = sh.U[tid * SSTRIDE + b];
         cbar();
-        if (tid == 0) { sh.force_b = -1; sh.force_sid = -1; }
-        for (int k = tid; k < np; k += NCT) sh.zb[k] = zval(k, sh.ub, 1, sh, f);
+        if (tid < np) zb[tid] = zval(tid, sh.ub, 1, sh, f);
         cbar();
         // x~ = W S(a,b) - U~[b] . z_a ;  y~ = W S(b,b) - U~[b] . z_b   (warp 0)
         if (warp == 0) {
             uint64_t ax = 0, ay = 0;
             for (int k = lane; k < np; k += 32) {
-                mac<true>(ax, sh.ub[k], sh.za[k], f);
-                mac<true>(ay, sh.ub[k], sh.zb[k], f);
+                mac<true>(ax, sh.ub[k], za[k], f);
+                mac<true>(ay, sh.ub[k], zb[k], f);
             }
             uint64_t sx = fp_reduce64(ax, f), sy = fp_reduce64(ay, f);
             for (int o = 16; o > 0; o >>= 1) {
@@ -666,36 +845,50 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
             }
         }
         // c~_b[t] for the window rows t >= a (overlaps warp 0's work)
-        const uint32_t cb_t = schur2<BIG>(P, sh.U, lr, lr, b, W, sh.zb, np, half, inwin && lr >= a, true);
+        const uint32_t s_b = myrow ? s_at(P.S, P.ldS, lr, b) : 0u;
+        const uint32_t cb_t = schur2<BIG>(P, sh.U, lr, lr, s_b, W, zb, np, half, myrow, true);
         cbar();
         const uint32_t x = sh.xy[0], y = sh.xy[1];
-        if (inwin && lr >= a && half == 0) {
+        if (myrow && half == 0) {
             sh.U[np * SSTRIDE + lr] = ca_t;  // c~_a[a] = 0 here
             sh.U[(np + 1) * SSTRIDE + lr] = cb_t;
             P.LpT[(int64_t)np * P.ldL + lr] = ca_t;
             P.LpT[(int64_t)(np + 1) * P.ldL + lr] = cb_t;
         }
         const uint32_t delta = fp_mul(W, fp_mul(x, x, f), f);
-        for (int k = tid; k < np; k += NCT)
-            if (sh.kind[k] != K_2B) sh.bw[k] = fp_mul(sh.bw[k], delta, f);
-        if (helpers && warp == 0) push_w0(EV_PIVOT2, a, b, np, W, 0, sh.za, sh.zb, nullptr, np);
+        if (tid < np && sh.kind[tid] != K_2B) sh.bw[tid] = fp_mul(sh.bw[tid], delta, f);
         if (tid == 0) {
+            if (helpers) {
+                Event &ev = sh.ev[slot];
+                ev.kind = EV_PIVOT2; ev.a = a; ev.b = b; ev.np = np; ev.s0 = W; ev.s1 = 0;
+                ev.scan_id = 0; ev.pad = 0;
+                __threadfence_block();
+                sh.ev_ready = ev_next + 1;
+            }
             sh.kind[np] = K_2A; sh.kind[np + 1] = K_2B;
             sh.bw[np] = W; sh.mx[np] = x; sh.my[np] = y; sh.piv[np] = x; sh.w0[np] = W;
-            sh.W = fp_mul(W, delta, f);
+            sh.delta[np] = delta;
             sh.piv_rows[np] = a; sh.piv_rows[np + 1] = b;
             sh.wstate[a] = 1;
             if (b < w) sh.wstate[b] = 1;
             P.consumed[b] = 1;
-            sh.np = np + 2; sh.ia = ia + 1;
-            check_scans();
         }
+        W = fp_mul(W, delta, f);
+        np += 2;
+        ++ia;
+        if (helpers) ++ev_next;
+        force_b = -1;
+        force_sid = -1;
         cbar();
-        lap(7);
+        lap(4);
     }
+    if (tid == 0) {
+        sh.np = np; sh.ia = ia; sh.nzero = nzero; sh.nscan = nscan; sh.nrollback = nrb;
+    }
+    cbar();
 
     // ---- end of panel: batch inversion, true D and the L coefficients ----
-    const int np = sh.np, iend = sh.ia, nzero = sh.nzero;
+    const int iend = ia;
     if (!sh.abort) {
         if (tid == 0) {
             // per block: its pivot value and its W, inverted together (Montgomery's trick)
@@ -742,7 +935,23 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
         if (helpers) {
             for (int k = tid; k < np; k += NCT) sh.bpre[k] = sh.kind[k];
             cbar();
-            if (warp == 0) push_w0(EV_END, -1, -1, np, 0, 0, sh.bpre, sh.cA, sh.cB, np);
+            // the end event carries the column kinds and the true-L coefficients
+            const int slot = ev_next % NSLOT;
+            if (tid < np) {
+                ring_ready(ev_next);
+                sh.ring[slot][tid] = sh.bpre[tid];
+                sh.ring[slot][KP_MAX + tid] = sh.cA[tid];
+                sh.ring[slot][2 * KP_MAX + tid] = sh.cB[tid];
+            }
+            if (tid == 0) ring_ready(ev_next);
+            cbar();
+            if (tid == 0) {
+                Event &ev = sh.ev[slot];
+                ev.kind = EV_END; ev.a = -1; ev.b = -1; ev.np = np; ev.s0 = 0; ev.s1 = 0;
+                ev.scan_id = 0; ev.pad = 0;
+                __threadfence_block();
+                sh.ev_ready = ev_next + 1;
+            }
         }
         // rewrite the window rows as true L columns
         for (int t = tid; t < w; t += NCT) finish_row(P, sh.U + t, SSTRIDE, P.LpT + t, np, sh.kind, sh.cA, sh.cB);
@@ -799,6 +1008,9 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
         P.out->nscan = sh.nscan;
         P.out->pad[0] = sh.nrollback;
         for (int i = 0; i < 8; ++i) P.out->cyc[i] = cyc[i];
+        sh.dbg[4] = sh.nrollback;
+        for (int i = 0; i < 16; ++i)
+            if (i < 5 || i > 7) P.out->dbg[i] = sh.dbg[i];
     }
 }
 

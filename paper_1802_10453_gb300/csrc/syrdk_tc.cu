@@ -106,11 +106,15 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int64_t
                                           volatile int *abort_flag)
 {
     if (mbar_try(bar, parity)) return true;
-    const int64_t t0 = gtime();
-    for (;;) {
+    int64_t t0 = 0;
+    for (unsigned n = 1;; ++n) {
         if (mbar_try(bar, parity)) return true;
-        if (*abort_flag) return false;
-        if (gtime() - t0 > budget) return false;
+        if ((n & 255u) == 0) {  // the abort flag and the clock are read once every 256 tries
+            if (*abort_flag) return false;
+            const int64_t t = gtime();
+            if (t0 == 0) t0 = t;
+            else if (t - t0 > budget) return false;
+        }
     }
 }
 
