@@ -41,6 +41,7 @@ extern "C" {
 #define LDLT_ERR_CUDA       -5  /* a CUDA runtime call failed (launch, copy, ...)  */
 #define LDLT_ERR_TIMEOUT    -6  /* device only: a bounded spin-wait gave up        */
 #define LDLT_ERR_NO_DEVICE  -7  /* no sm_103 device visible                         */
+#define LDLT_ERR_TOO_LARGE  -8  /* n above LDLT_NOALLOC_MAX_N (no-allocation entry) */
 
 /* ---- arithmetic paths for the level-3 updates (SYRDK, Algorithm 2) ------ */
 /* FP64 form: residues carried in doubles, products accumulated with one
@@ -107,6 +108,45 @@ int ldlt_rpm_factor(int64_t n, uint32_t p, uint32_t *A, int64_t lda,
  */
 int rpm_from_factor(int64_t n, const int32_t *perm, const uint32_t *e,
                     const int64_t *rank, int32_t *rpm_col, void *stream);
+
+/*
+ * ldlt_rpm_factor_noalloc -- ldlt_rpm_factor for callers that must not
+ * allocate device memory at call time.  The paper has no counterpart: it is a
+ * packaging of the same factorisation, not a step of the method.
+ *
+ * Some callers cannot hand the library a workspace: a plain C program that
+ * has given all of its device memory to its own pool, or a latency-critical
+ * loop in which a cudaMalloc (which may synchronise the whole device) is not
+ * acceptable.  This entry point takes the arguments of ldlt_rpm_factor minus
+ * ws / ws_bytes and runs the same kernels with their scratch in one
+ * file-scope device array of LDLT_NOALLOC_BYTES bytes that is part of the
+ * library.  It calls no cudaMalloc / cudaFree and no allocating library
+ * routine.
+ *
+ *   n        0 <= n <= LDLT_NOALLOC_MAX_N; a larger n returns
+ *            LDLT_ERR_TOO_LARGE before any device work.
+ *   others   exactly as for ldlt_rpm_factor (same outputs, bit for bit).
+ *
+ * First call on a device: with that device current, the call looks up the
+ * array's device address once (cudaGetSymbolAddress) and remembers it for
+ * that device; later calls reuse it.  Make that first call before any stream
+ * capture begins.  CUDA reserves the array's memory when it loads the module
+ * that holds it; with CUDA's default lazy module loading that happens at this
+ * first call, not when the library is opened.
+ *
+ * Every call on a device uses the same array.  The factorisation clears, on
+ * the stream, every part of its scratch that must start at zero, so one call
+ * leaves nothing that a later call depends on; but calls that overlap in time
+ * on one device (two streams, or two host threads) race on the array and give
+ * undefined results.  Serialise them.
+ *
+ * Returns what ldlt_rpm_factor returns, or LDLT_ERR_TOO_LARGE.
+ */
+#define LDLT_NOALLOC_MAX_N  1024
+#define LDLT_NOALLOC_BYTES  ((size_t)48 << 20)
+int ldlt_rpm_factor_noalloc(int64_t n, uint32_t p, uint32_t *A, int64_t lda,
+                            int32_t *perm, uint32_t *e, int64_t *rank,
+                            int32_t *status, int path, void *stream);
 
 /*
  * ldlt_rpm_version -- library version as major*10000 + minor*100 + patch.

@@ -19,12 +19,16 @@ from .binding import (  # noqa: F401
     LDLT_ERR_CUDA,
     LDLT_ERR_TIMEOUT,
     LDLT_ERR_NO_DEVICE,
+    LDLT_ERR_TOO_LARGE,
+    NOALLOC_MAX_N,
+    NOALLOC_BYTES,
     LdltError,
     lib,
     lib_path,
     workspace_bytes,
     factor,
     factor_raw,
+    factor_noalloc,
     rpm_from_factor,
     set_wait_budget_ns,
     set_speculation,

@@ -23,12 +23,16 @@ LDLT_ERR_WORKSPACE = -4
 LDLT_ERR_CUDA = -5
 LDLT_ERR_TIMEOUT = -6
 LDLT_ERR_NO_DEVICE = -7
+LDLT_ERR_TOO_LARGE = -8
 _NAMES = {0: "LDLT_OK", -1: "LDLT_ERR_ARG", -2: "LDLT_ERR_NOT_PRIME", -3: "LDLT_ERR_P_RANGE",
           -4: "LDLT_ERR_WORKSPACE", -5: "LDLT_ERR_CUDA", -6: "LDLT_ERR_TIMEOUT",
-          -7: "LDLT_ERR_NO_DEVICE"}
+          -7: "LDLT_ERR_NO_DEVICE", -8: "LDLT_ERR_TOO_LARGE"}
+# largest order and scratch size of ldlt_rpm_factor_noalloc (LDLT_NOALLOC_* in the header)
+NOALLOC_MAX_N = 1024
+NOALLOC_BYTES = 48 << 20
 
 EXPORTS = ["ldlt_rpm_workspace_bytes", "ldlt_rpm_factor", "rpm_from_factor", "ldlt_rpm_version",
-           "ldlt_rpm_set_wait_budget_ns", "ldlt_rpm_set_speculation"]
+           "ldlt_rpm_set_wait_budget_ns", "ldlt_rpm_set_speculation", "ldlt_rpm_factor_noalloc"]
 
 
 class LdltError(RuntimeError):
@@ -60,6 +64,9 @@ def lib():
             L.ldlt_rpm_factor.restype = ctypes.c_int
             L.ldlt_rpm_factor.argtypes = [c_i64, c_u32, c_vp, c_i64, c_vp, c_vp, c_vp, c_vp,
                                           ctypes.c_int, c_vp, c_sz, c_vp]
+            L.ldlt_rpm_factor_noalloc.restype = ctypes.c_int
+            L.ldlt_rpm_factor_noalloc.argtypes = [c_i64, c_u32, c_vp, c_i64, c_vp, c_vp, c_vp, c_vp,
+                                                  ctypes.c_int, c_vp]
             L.rpm_from_factor.restype = ctypes.c_int
             L.rpm_from_factor.argtypes = [c_i64, c_vp, c_vp, c_vp, c_vp, c_vp]
             L.ldlt_rpm_version.restype = ctypes.c_int
@@ -150,6 +157,39 @@ def factor(A, p: int, path: int = PATH_TC, stream=None, workspace=None, check: b
         if st != 0:
             raise LdltError(st, "device status")
     return res
+
+
+def factor_noalloc(A, p: int, perm, e, rank, status, path: int = PATH_TC, stream=None) -> dict:
+    """ldlt_rpm_factor_noalloc: factor A in place like factor(), with the
+    library's own fixed scratch array instead of a workspace, for callers that
+    must not allocate device memory at call time (n <= NOALLOC_MAX_N).
+
+    The caller supplies the outputs (perm, e: int32[n]; rank: int64[1];
+    status: int32[1], all on A's device); this wrapper only passes pointers and
+    neither allocates nor synchronises.  Calls on one device share the scratch
+    array, so calls that overlap in time race; the first call on a device looks
+    up the array's address and should come before any stream capture.
+    Returns dict(perm, e, rank, status, n, p); read status after the stream.
+    """
+    import torch
+    if not A.is_cuda or A.dtype != torch.int32 or A.dim() != 2 or A.shape[0] != A.shape[1]:
+        raise LdltError(LDLT_ERR_ARG, "A must be a square int32 CUDA tensor")
+    n = A.shape[0]
+    if n > 0 and A.stride(1) != 1:
+        raise LdltError(LDLT_ERR_ARG, "rows of A must be contiguous")
+    for t, dt, cnt in ((perm, torch.int32, n), (e, torch.int32, n), (rank, torch.int64, 1),
+                       (status, torch.int32, 1)):
+        if t.device != A.device or t.dtype != dt or t.numel() < cnt or not t.is_contiguous():
+            raise LdltError(LDLT_ERR_ARG, "output tensors: perm/e int32[n], rank int64[1], status int32[1]")
+    if stream is None:
+        stream = torch.cuda.current_stream(A.device)
+    lda = A.stride(0) if n > 0 else 1
+    rc = lib().ldlt_rpm_factor_noalloc(int(n), int(p), A.data_ptr(), int(lda), perm.data_ptr(),
+                                       e.data_ptr(), rank.data_ptr(), status.data_ptr(), int(path),
+                                       stream.cuda_stream)
+    if rc != LDLT_OK:
+        raise LdltError(rc, "ldlt_rpm_factor_noalloc")
+    return dict(perm=perm, e=e, rank=rank, status=status, n=n, p=p)
 
 
 def rpm_from_factor(res: dict, stream=None):

@@ -21,7 +21,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]
 
 LIBS = {
-    "libldlt_rpm.so": ["panel.cu", "kernels_misc.cu", "syrdk_fp64.cu", "syrdk_tc.cu", "ldlt_rpm.cu"],
+    "libldlt_rpm.so": ["panel.cu", "kernels_misc.cu", "syrdk_fp64.cu", "syrdk_tc.cu", "ldlt_rpm.cu",
+                       "noalloc.cu"],
     "libldlt_gen.so": ["gen_kernels.cu"],
 }
 HEADERS = ["field.cuh", "ldlt_internal.cuh"]

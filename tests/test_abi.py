@@ -74,3 +74,28 @@ def test_effective_ops_formula(libs):
     # Section 6: r^3/3 + n^2 r - r^2 n; r = n gives n^3/3
     assert libs.effective_ops(300, 300) == pytest.approx(300 ** 3 / 3)
     assert libs.effective_ops(16384, 8192) == pytest.approx(7 * 16384 ** 3 / 24)
+
+
+def test_noalloc_limits_on_host(libs):
+    """ldlt_rpm_factor_noalloc refuses what its fixed scratch array cannot hold
+    before touching the device, and that array holds every problem up to the
+    stated maximum order on both paths."""
+    hdr = open(os.path.join(ROOT, "include", "ldlt_rpm.h")).read()
+    assert int(re.search(r"#define LDLT_NOALLOC_MAX_N\s+(\d+)", hdr).group(1)) == libs.NOALLOC_MAX_N
+    mb = int(re.search(r"#define LDLT_NOALLOC_BYTES\s+\(\(size_t\)(\d+) << 20\)", hdr).group(1))
+    assert mb << 20 == libs.NOALLOC_BYTES
+    assert int(re.search(r"#define LDLT_ERR_TOO_LARGE\s+(-\d+)", hdr).group(1)) == libs.LDLT_ERR_TOO_LARGE
+    for p in (2, 3, 251, 65521, 8388593, 67108859, 2147483647):
+        for path in (libs.PATH_FP64, libs.PATH_TC):
+            try:
+                need = libs.workspace_bytes(libs.NOALLOC_MAX_N, p, path)
+            except libs.LdltError:
+                continue
+            assert need <= libs.NOALLOC_BYTES, (p, path, need)
+    L = libs.lib()
+    buf = ctypes.create_string_buffer(8)
+    big = libs.NOALLOC_MAX_N + 1
+    assert L.ldlt_rpm_factor_noalloc(big, 65521, buf, big, buf, buf, buf, buf, 1, None) == -8
+    assert L.ldlt_rpm_factor_noalloc(4, 15, buf, 4, buf, buf, buf, buf, 1, None) == -2
+    assert L.ldlt_rpm_factor_noalloc(-1, 7, buf, 4, buf, buf, buf, buf, 1, None) == -1
+    assert L.ldlt_rpm_factor_noalloc(4, 7, buf, 4, buf, buf, buf, buf, 5, None) == -1
