@@ -110,6 +110,69 @@ int rpm_from_factor(int64_t n, const int32_t *perm, const uint32_t *e,
                     const int64_t *rank, int32_t *rpm_col, void *stream);
 
 /*
+ * ldlt_rpm_factor_batched -- factor `count` independent matrices, each as
+ * ldlt_rpm_factor does (same pivot order, same outputs bit for bit), in one
+ * persistent launch: the batched use of the method that Section 6 discusses
+ * (many problems whose order is below the recursion threshold).  Every CTA
+ * factors whole matrices taken from a queue in order of decreasing n; a
+ * matrix never leaves its SM.
+ *
+ *   count    number of matrices (0 <= count <= INT_MAX).
+ *   n        int64[count] (device): orders, 0 <= n[i] <= LDLT_BATCH_MAX_N.
+ *   p        prime modulus shared by all matrices, as for ldlt_rpm_factor.
+ *   A        uint32*[count] (device array of device pointers): matrix i,
+ *            row-major with leading dimension lda[i] >= n[i]; input and output
+ *            as for ldlt_rpm_factor.
+ *   lda      int64[count] (device).
+ *   perm     int32*[count], e uint32*[count] (device arrays of device
+ *            pointers): outputs as for ldlt_rpm_factor, n[i] entries each.
+ *   rank     int64[count] (device): ranks.
+ *   status   int32[count] (device): 0, or LDLT_ERR_ARG for a matrix whose
+ *            n, lda or pointers are invalid (that matrix is left untouched;
+ *            the others are factored).
+ *   path     LDLT_PATH_FP64 or LDLT_PATH_TC, validated as for
+ *            ldlt_rpm_factor.  Matrices of order <= 512 are bound by the
+ *            pivot chain, not by the update products, so both values run the
+ *            same exact integer arithmetic on the CUDA cores.
+ *   ws       device workspace, 256-byte aligned: at least the header plus one
+ *            CTA's scratch (2 MiB); ldlt_rpm_batched_workspace_bytes gives the
+ *            size that lets every resident CTA run.  A smaller workspace runs
+ *            fewer CTAs.
+ *   stream   cudaStream_t as void*.
+ *
+ * Enqueues three operations on `stream` (a memset and two kernels) and
+ * returns without synchronising; nothing is read back to the host.  Returns
+ * LDLT_OK, LDLT_ERR_ARG, LDLT_ERR_NOT_PRIME, LDLT_ERR_P_RANGE,
+ * LDLT_ERR_WORKSPACE, LDLT_ERR_CUDA or LDLT_ERR_NO_DEVICE.
+ */
+#define LDLT_BATCH_MAX_N    512
+int ldlt_rpm_factor_batched(int64_t count, const int64_t *n, uint32_t p,
+                            uint32_t *const *A, const int64_t *lda,
+                            int32_t *const *perm, uint32_t *const *e,
+                            int64_t *rank, int32_t *status, int path,
+                            void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * ldlt_rpm_batched_workspace_bytes -- workspace of ldlt_rpm_factor_batched
+ * for `count` matrices: a header (queue counter, queue order) and 2 MiB of
+ * scratch for each CTA that can run (at most min(count, 640)).  Pure host
+ * computation.  Returns LDLT_OK, LDLT_ERR_ARG, LDLT_ERR_NOT_PRIME or
+ * LDLT_ERR_P_RANGE.
+ */
+int ldlt_rpm_batched_workspace_bytes(int64_t count, uint32_t p, int path, size_t *bytes);
+
+/*
+ * ldlt_rpm_batched_set_schedule -- tile and cutoff choices of the batched
+ * schedule (process-wide; picked by the package's autotuner): kb = 16, 32 or
+ * 64 is the largest number of pivots per panel the kernel is built for (it
+ * fixes shared memory and so the CTAs per SM); matrices with n < n_cut use
+ * panels of kb_small (4 <= kb_small <= kb) pivots instead.  Results do not
+ * depend on these choices.  Default (32, 0, 32).  Returns LDLT_OK or
+ * LDLT_ERR_ARG.
+ */
+int ldlt_rpm_batched_set_schedule(int kb, int n_cut, int kb_small);
+
+/*
  * ldlt_rpm_factor_noalloc -- ldlt_rpm_factor for callers that must not
  * allocate device memory at call time.  The paper has no counterpart: it is a
  * packaging of the same factorisation, not a step of the method.

@@ -29,6 +29,11 @@ from .binding import (  # noqa: F401
     factor,
     factor_raw,
     factor_noalloc,
+    factor_batched,
+    batched_workspace_bytes,
+    set_batched_schedule,
+    Batch,
+    BATCH_MAX_N,
     rpm_from_factor,
     set_wait_budget_ns,
     set_speculation,

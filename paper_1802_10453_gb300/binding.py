@@ -32,7 +32,9 @@ NOALLOC_MAX_N = 1024
 NOALLOC_BYTES = 48 << 20
 
 EXPORTS = ["ldlt_rpm_workspace_bytes", "ldlt_rpm_factor", "rpm_from_factor", "ldlt_rpm_version",
-           "ldlt_rpm_set_wait_budget_ns", "ldlt_rpm_set_speculation", "ldlt_rpm_factor_noalloc"]
+           "ldlt_rpm_set_wait_budget_ns", "ldlt_rpm_set_speculation", "ldlt_rpm_factor_noalloc",
+           "ldlt_rpm_factor_batched", "ldlt_rpm_batched_workspace_bytes", "ldlt_rpm_batched_set_schedule"]
+BATCH_MAX_N = 512  # LDLT_BATCH_MAX_N
 
 
 class LdltError(RuntimeError):
@@ -67,6 +69,13 @@ def lib():
             L.ldlt_rpm_factor_noalloc.restype = ctypes.c_int
             L.ldlt_rpm_factor_noalloc.argtypes = [c_i64, c_u32, c_vp, c_i64, c_vp, c_vp, c_vp, c_vp,
                                                   ctypes.c_int, c_vp]
+            L.ldlt_rpm_factor_batched.restype = ctypes.c_int
+            L.ldlt_rpm_factor_batched.argtypes = [c_i64, c_vp, c_u32, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp,
+                                                  ctypes.c_int, c_vp, c_sz, c_vp]
+            L.ldlt_rpm_batched_workspace_bytes.restype = ctypes.c_int
+            L.ldlt_rpm_batched_workspace_bytes.argtypes = [c_i64, c_u32, ctypes.c_int, ctypes.POINTER(c_sz)]
+            L.ldlt_rpm_batched_set_schedule.restype = ctypes.c_int
+            L.ldlt_rpm_batched_set_schedule.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
             L.rpm_from_factor.restype = ctypes.c_int
             L.rpm_from_factor.argtypes = [c_i64, c_vp, c_vp, c_vp, c_vp, c_vp]
             L.ldlt_rpm_version.restype = ctypes.c_int
@@ -190,6 +199,102 @@ def factor_noalloc(A, p: int, perm, e, rank, status, path: int = PATH_TC, stream
     if rc != LDLT_OK:
         raise LdltError(rc, "ldlt_rpm_factor_noalloc")
     return dict(perm=perm, e=e, rank=rank, status=status, n=n, p=p)
+
+
+def batched_workspace_bytes(count: int, p: int, path: int = PATH_TC) -> int:
+    out = ctypes.c_size_t(0)
+    rc = lib().ldlt_rpm_batched_workspace_bytes(int(count), int(p), int(path), ctypes.byref(out))
+    if rc != LDLT_OK:
+        raise LdltError(rc, "batched workspace query")
+    return int(out.value)
+
+
+def set_batched_schedule(kb: int, n_cut: int = 0, kb_small: int | None = None) -> None:
+    rc = lib().ldlt_rpm_batched_set_schedule(int(kb), int(n_cut), int(kb if kb_small is None else kb_small))
+    if rc != LDLT_OK:
+        raise LdltError(rc, "batched schedule: kb in {16, 32, 64}, 0 <= n_cut <= 513, 4 <= kb_small <= kb")
+
+
+class Batch:
+    """Device buffers for a batch of matrices, back to back in one int32 arena.
+
+    matrix(i) is the (n_i, n_i) view of matrix i (leading dimension n_i);
+    perm(i), e(i) its outputs; rank and status hold one entry per matrix.  The
+    pointer and order arrays the C ABI takes are built once here."""
+
+    def __init__(self, ns, device="cuda"):
+        import numpy as np
+        import torch
+        self.ns = [int(x) for x in ns]
+        self.count = len(self.ns)
+        dev = torch.device(device)
+        sq = np.array([max(v, 0) ** 2 for v in self.ns], dtype=np.int64)
+        lin = np.array([max(v, 0) for v in self.ns], dtype=np.int64)
+        self._aoff = np.concatenate([[0], np.cumsum(sq)])
+        self._poff = np.concatenate([[0], np.cumsum(lin)])
+        self.arena = torch.zeros(max(int(self._aoff[-1]), 1), dtype=torch.int32, device=dev)
+        self.perm_arena = torch.full((max(int(self._poff[-1]), 1),), -1, dtype=torch.int32, device=dev)
+        self.e_arena = torch.zeros(max(int(self._poff[-1]), 1), dtype=torch.int32, device=dev)
+        self.rank = torch.zeros(max(self.count, 1), dtype=torch.int64, device=dev)
+        self.status = torch.zeros(max(self.count, 1), dtype=torch.int32, device=dev)
+
+        def ptrs(t, offs):
+            return torch.tensor([t.data_ptr() + 4 * int(o) for o in offs[:-1]] or [0], dtype=torch.int64,
+                                device=dev)
+
+        self.A_ptrs = ptrs(self.arena, self._aoff)
+        self.perm_ptrs = ptrs(self.perm_arena, self._poff)
+        self.e_ptrs = ptrs(self.e_arena, self._poff)
+        self.n = torch.tensor(self.ns or [0], dtype=torch.int64, device=dev)
+        self.lda = torch.tensor([max(v, 1) for v in self.ns] or [1], dtype=torch.int64, device=dev)
+
+    def matrix(self, i):
+        n = self.ns[i]
+        return self.arena[int(self._aoff[i]):int(self._aoff[i + 1])].view(n, n)
+
+    def perm(self, i):
+        return self.perm_arena[int(self._poff[i]):int(self._poff[i + 1])]
+
+    def e(self, i):
+        return self.e_arena[int(self._poff[i]):int(self._poff[i + 1])]
+
+
+_bws_cache = {}
+
+
+def factor_batched(batch: "Batch", p: int, path: int = PATH_TC, stream=None, workspace=None,
+                   check: bool = True):
+    """ldlt_rpm_factor_batched over every matrix of `batch`, in place.
+
+    Raises LdltError for a host-detected error; with check=True waits for the
+    stream and raises if any matrix's status is non-zero.  Returns the status
+    tensor (one int32 per matrix)."""
+    import torch
+    dev = batch.arena.device
+    if workspace is None:
+        nbytes = batched_workspace_bytes(batch.count, p, path)
+        key = str(dev)
+        buf = _bws_cache.get(key)
+        if buf is None or buf.numel() < nbytes:
+            buf = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=dev)
+            _bws_cache[key] = buf
+        workspace = buf
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    rc = lib().ldlt_rpm_factor_batched(batch.count, batch.n.data_ptr(), int(p), batch.A_ptrs.data_ptr(),
+                                       batch.lda.data_ptr(), batch.perm_ptrs.data_ptr(),
+                                       batch.e_ptrs.data_ptr(), batch.rank.data_ptr(),
+                                       batch.status.data_ptr(), int(path), workspace.data_ptr(),
+                                       workspace.numel(), stream.cuda_stream)
+    if rc != LDLT_OK:
+        raise LdltError(rc, "ldlt_rpm_factor_batched")
+    if check:
+        stream.synchronize()
+        bad = (batch.status[:batch.count] != 0).nonzero()
+        if bad.numel():
+            i = int(bad[0, 0])
+            raise LdltError(int(batch.status[i].item()), "matrix %d of the batch" % i)
+    return batch.status
 
 
 def rpm_from_factor(res: dict, stream=None):

@@ -19,6 +19,8 @@ Workloads (the matrix families of the paper's Section 6 experiments):
   rank, so the rank profile matrix of A is supp(R).
 * uniform symmetric: entries i.i.d. uniform in [0, p) mirrored (generic rank
   profile with high probability).
+* batch: many independent planted matrices of uneven order n_i and rank r_i
+  (orders below the recursion threshold of Section 6).
 """
 from __future__ import annotations
 
@@ -34,6 +36,7 @@ TAG_T = 1      # entries of T
 TAG_SUPPORT = 2  # choice and pairing of the support of R
 TAG_SCALE = 3  # scalings of R
 TAG_UNIFORM = 4  # uniform symmetric matrix
+TAG_BATCH = 5  # orders and ranks of the matrices of a batch
 
 
 def mix64_scalar(z: int) -> int:
@@ -170,11 +173,33 @@ def default_pairs(r: int, all_pairs: bool = False) -> int:
     return r // 2 if all_pairs else r // 4
 
 
+def batch_shapes(count: int, n_lo: int, n_hi: int, seed: int):
+    """Orders n_i uniform in [n_lo, n_hi] and ranks r_i uniform in
+    [ceil(n_i / 4), n_i] for a batch of `count` matrices (batch stream outputs
+    2i and 2i + 1); matrix i is planted with seed ``batch_seed(seed, i)``."""
+    key = derive_key(seed, TAG_BATCH)
+    u = stream(key, np.arange(2 * count, dtype=np.uint64)) >> np.uint64(32)
+    u = u.astype(np.int64)
+    n = n_lo + ((u[0::2] * (n_hi - n_lo + 1)) >> 32)
+    rlo = (n + 3) // 4
+    r = rlo + ((u[1::2] * (n - rlo + 1)) >> 32)
+    return n.astype(np.int64), r.astype(np.int64)
+
+
+def batch_seed(seed: int, i: int) -> int:
+    return (int(seed) << 24) + int(i)
+
+
 # Named workloads: (kind, n, r, p, all_pairs).  Seeds are 180210453 + index.
 WORKLOADS = {
     "planted_n256_r192_p65521": ("planted", 256, 192, 65521, False),
     "uniform_n4096_p8388593": ("uniform", 4096, 4096, 8388593, False),
     "planted_n16384_r8192_p67108859": ("planted", 16384, 8192, 67108859, False),
     "planted_n32768_r16384_p2147483647_pairs": ("planted", 32768, 16384, 2147483647, True),
+}
+# Batch of independent planted matrices: (count, n_lo, n_hi, p); ranks
+# uniform in [n/4, n], floor(r/4) pairs each.
+BATCH_WORKLOADS = {
+    "batch4096_n32to512_p65521": (4096, 32, 512, 65521),
 }
 SEED_BASE = 180210453

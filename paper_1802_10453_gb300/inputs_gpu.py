@@ -71,6 +71,38 @@ def planted_matrix(n, r, npairs, p, seed, device="cuda", out=None):
     return A, partner
 
 
+def planted_batch(batch, rs, p, seed, all_pairs=False):
+    """Fill every matrix of a binding.Batch with its planted matrix: matrix i
+    has order batch.ns[i], rank rs[i], default_pairs(rs[i]) pairs and seed
+    inputs.batch_seed(seed, i).  Returns the list of partner arrays."""
+    import torch
+    L = _load()
+    dev = batch.arena.device
+    st = torch.cuda.current_stream(dev)
+    nmax = max(batch.ns) if batch.ns else 0
+    ws = torch.empty(max(int(L.ldlt_gen_planted_ws_bytes(nmax, nmax)), 256), dtype=torch.uint8, device=dev)
+    keep, partners = [], []
+    for i, n in enumerate(batch.ns):
+        r = int(rs[i])
+        s_i = inputs.batch_seed(seed, i)
+        partner, scale = inputs.planted_support(n, r, inputs.default_pairs(r, all_pairs), p, s_i)
+        kq, pq, sq = planted_terms(partner, scale)
+        kq_t = torch.from_numpy(kq).to(dev, non_blocking=False)
+        pq_t = torch.from_numpy(pq).to(dev)
+        sq_t = torch.from_numpy(sq.view(np.int32)).to(dev)
+        keep.append((kq_t, pq_t, sq_t))
+        A = batch.matrix(i)
+        rc = L.ldlt_gen_planted(n, p, inputs.derive_key(s_i, inputs.TAG_T), len(kq), kq_t.data_ptr(),
+                                pq_t.data_ptr(), sq_t.data_ptr(), A.data_ptr(), max(n, 1), ws.data_ptr(),
+                                st.cuda_stream)
+        if rc != 0:
+            raise RuntimeError("ldlt_gen_planted failed: %d" % rc)
+        partners.append(partner)
+    st.synchronize()
+    del keep, ws
+    return partners
+
+
 def uniform_symmetric(n, p, seed, device="cuda", out=None):
     import torch
     A = out if out is not None else torch.zeros((n, n), dtype=torch.int32, device=device)

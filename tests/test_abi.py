@@ -99,3 +99,26 @@ def test_noalloc_limits_on_host(libs):
     assert L.ldlt_rpm_factor_noalloc(4, 15, buf, 4, buf, buf, buf, buf, 1, None) == -2
     assert L.ldlt_rpm_factor_noalloc(-1, 7, buf, 4, buf, buf, buf, buf, 1, None) == -1
     assert L.ldlt_rpm_factor_noalloc(4, 7, buf, 4, buf, buf, buf, buf, 5, None) == -1
+
+
+def test_batched_host_checks(libs):
+    """ldlt_rpm_factor_batched rejects bad arguments before any device work."""
+    L = libs.lib()
+    buf = ctypes.create_string_buffer(1024)
+    args = lambda count, p, path, ws, nbytes: (count, buf, p, buf, buf, buf, buf, buf, buf, path, ws, nbytes, None)
+    assert L.ldlt_rpm_factor_batched(*args(-1, 7, 1, buf, 1024)) == -1
+    assert L.ldlt_rpm_factor_batched(*args(3, 15, 1, buf, 1024)) == -2
+    assert L.ldlt_rpm_factor_batched(*args(3, 2147483659, 1, buf, 1024)) == -3
+    assert L.ldlt_rpm_factor_batched(*args(3, 7, 9, buf, 1024)) == -1
+    assert L.ldlt_rpm_factor_batched(*args(0, 7, 1, None, 0)) == 0          # nothing to do
+    assert L.ldlt_rpm_factor_batched(*args(3, 7, 1, None, 0)) == -4
+    assert L.ldlt_rpm_factor_batched(*args(3, 7, 1, buf, 1024)) == -4      # less than one CTA's scratch
+    assert L.ldlt_rpm_factor_batched(3, None, 7, buf, buf, buf, buf, buf, buf, 1, buf, 1024, None) == -1
+    one = 2 * 512 * 512 * 4
+    assert libs.batched_workspace_bytes(1, 65521) == 256 + 256 + one
+    assert libs.batched_workspace_bytes(4096, 65521) == 256 + 4096 * 4 + 640 * one
+    with pytest.raises(libs.LdltError):
+        libs.batched_workspace_bytes(5, 65520)
+    for bad in [(8, 0, 8), (32, -1, 32), (32, 514, 32), (32, 0, 3), (16, 0, 32)]:
+        assert L.ldlt_rpm_batched_set_schedule(*bad) == -1
+    assert L.ldlt_rpm_batched_set_schedule(32, 0, 32) == 0

@@ -163,32 +163,48 @@ def test_config1_uniform_n4096(path):
     assert_parity(A, p, PATHS[path])
 
 
-def _freivalds_host(Alow, perm, Lstrict, d, e, p, trials=2, seed=99):
-    """P^T A P x == L (D (L^T x)) mod p for random x; A given by its lower part."""
-    rng = np.random.default_rng(seed)
-    n = Alow.shape[0]
-    Lm = Lstrict.copy()
-    Lm[np.arange(n), np.arange(n)] = 1
+def _freivalds_host(A32, L32, perm, d, e, p, trials=2, seed=99, block=1024):
+    """P^T A P x == L (D (L^T x)) mod p for random x, exact in int64.
 
-    def mv(M, x):  # exact (M @ x) mod p, x split in 16-bit halves
+    A32: the input, only its lower triangle is used; L32: the returned matrix,
+    only its strict lower triangle (L) is used.  Both are processed in blocks
+    of rows so that n = 32768 fits in host memory."""
+    rng = np.random.default_rng(seed)
+    n = A32.shape[0]
+
+    def mulv(M, x):  # exact (M @ x) mod p for entries < 2^31, x split in 16-bit halves
         lo, hi = x & 0xFFFF, x >> 16
         return ((((M @ hi) % p) << 16) % p + (M @ lo) % p) % p
+
+    def low_mv(M32, x, strict, transpose):
+        y = np.zeros(n, dtype=np.int64)
+        for i0 in range(0, n, block):
+            i1 = min(n, i0 + block)
+            blk = M32[i0:i1, :i1].astype(np.int64) & 0xFFFFFFFF
+            rows = np.arange(i0, i1)[:, None]
+            cols = np.arange(i1)[None, :]
+            blk[(cols >= rows) if strict else (cols > rows)] = 0
+            if transpose:
+                y[:i1] = (y[:i1] + mulv(blk.T, x[i0:i1])) % p
+            else:
+                y[i0:i1] = mulv(blk, x[:i1])
+        return y
 
     for _ in range(trials):
         x = rng.integers(0, p, size=n, dtype=np.int64)
         px = np.zeros(n, dtype=np.int64)
         px[perm] = x
         # S px with S symmetric from its lower part: (low + strict_low^T) px
-        lhs = (mv(Alow, px) + mv(np.tril(Alow, -1).T.copy(), px)) % p
+        lhs = (low_mv(A32, px, False, False) + low_mv(A32, px, True, True)) % p
         lhs = lhs[perm]
-        t = mv(Lm.T.copy(), x)
+        t = (low_mv(L32, x, True, True) + x) % p                 # L^T x (unit diagonal)
         Dt = (d * t) % p
         nxt = np.zeros(n, dtype=np.int64)
         nxt[:-1] = t[1:]
         prv = np.zeros(n, dtype=np.int64)
         prv[1:] = t[:-1] * e[:-1]
         Dt = (Dt + (e * nxt) % p + prv % p) % p
-        rhs = mv(Lm, Dt)
+        rhs = (low_mv(L32, Dt, True, False) + Dt) % p           # L (D L^T x)
         if not np.array_equal(lhs, rhs):
             return False
     return True
@@ -197,14 +213,15 @@ def _freivalds_host(Alow, perm, Lstrict, d, e, p, trials=2, seed=99):
 def _check_planted_full_size(n, r, all_pairs, p, seed, path):
     from paper_1802_10453_gb300 import inputs_gpu
     Ad, partner = inputs_gpu.planted_matrix(n, r, inputs.default_pairs(r, all_pairs), p, seed)
-    Alow = np.tril(Ad.cpu().numpy().astype(np.int64))
+    A32 = Ad.cpu().numpy()
     res = lr.factor(Ad, p, path=path)
     rpm = lr.rpm_from_factor(res).cpu().numpy().astype(np.int64)
-    out = Ad.cpu().numpy().astype(np.int64) & 0xFFFFFFFF
+    out32 = Ad.cpu().numpy()
+    del Ad
     perm = res["perm"].cpu().numpy().astype(np.int64)
     e = res["e"].cpu().numpy().astype(np.int64) & 0xFFFFFFFF
     rank = int(res["rank"].item())
-    d = np.diag(out).copy()
+    d = np.diag(out32).astype(np.int64) & 0xFFFFFFFF
     assert rank == r
     assert np.array_equal(rpm, partner)                       # reveals R_A = supp(R)
     perm_c, starts = o.canonical_perm_from_rpm(o.rpm_col_to_matrix(partner)) if n <= 4096 else \
@@ -214,8 +231,10 @@ def _check_planted_full_size(n, r, all_pairs, p, seed, path):
     if p != 2:
         assert np.all(d[np.roll(starts, 1)] == 0)             # antidiagonal blocks
     assert np.all(d[r:] == 0) and np.all(e[r:] == 0)
-    assert np.all(np.tril(out, -1)[r:, r:] == 0)              # identity columns beyond r
-    assert _freivalds_host(Alow, perm, np.tril(out, -1), d, e, p)
+    for i0 in range(r, n, 2048):                              # identity columns beyond r
+        blk = out32[i0:i0 + 2048, r:]
+        assert not np.any(np.tril(blk, i0 - r - 1))
+    assert _freivalds_host(A32, out32, perm, d, e, p)
 
 
 def _canonical_perm_sparse(partner):
@@ -244,6 +263,13 @@ def test_planted_n2048_properties_and_exact(path):
 def test_config2_planted_n16384_tc():
     """n = 16384, r = 8192, p = 2^26 - 5, 2048 pairs + 4096 fixed points."""
     _check_planted_full_size(16384, 8192, False, 67108859, inputs.SEED_BASE + 2, lr.PATH_TC)
+
+
+def test_config4_planted_n32768_all_pairs_tc():
+    """n = 32768, r = 16384, p = 2^31 - 1, R made only of transpositions
+    (8192 pairs, no fixed points): every pivot is a 2x2 antidiagonal block and
+    half of the rows are zero rows found by the far scans."""
+    _check_planted_full_size(32768, 16384, True, 2147483647, inputs.SEED_BASE + 4, lr.PATH_TC)
 
 
 def test_wait_budget_timeout_reports_status():
