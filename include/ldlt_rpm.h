@@ -135,9 +135,10 @@ int rpm_from_factor(int64_t n, const int32_t *perm, const uint32_t *e,
  *            pivot chain, not by the update products, so both values run the
  *            same exact integer arithmetic on the CUDA cores.
  *   ws       device workspace, 256-byte aligned: at least the header plus one
- *            CTA's scratch (2 MiB); ldlt_rpm_batched_workspace_bytes gives the
+ *            CTA's scratch (1 MiB); ldlt_rpm_batched_workspace_bytes gives the
  *            size that lets every resident CTA run.  A smaller workspace runs
- *            fewer CTAs.
+ *            fewer CTAs.  While a matrix is factored, the lower triangle of its
+ *            A holds its Schur complement; the upper triangle is not touched.
  *   stream   cudaStream_t as void*.
  *
  * Enqueues three operations on `stream` (a memset and two kernels) and
@@ -154,7 +155,7 @@ int ldlt_rpm_factor_batched(int64_t count, const int64_t *n, uint32_t p,
 
 /*
  * ldlt_rpm_batched_workspace_bytes -- workspace of ldlt_rpm_factor_batched
- * for `count` matrices: a header (queue counter, queue order) and 2 MiB of
+ * for `count` matrices: a header (queue counter, queue order) and 1 MiB of
  * scratch for each CTA that can run (at most min(count, 640)).  Pure host
  * computation.  Returns LDLT_OK, LDLT_ERR_ARG, LDLT_ERR_NOT_PRIME or
  * LDLT_ERR_P_RANGE.

@@ -114,7 +114,7 @@ def test_batched_host_checks(libs):
     assert L.ldlt_rpm_factor_batched(*args(3, 7, 1, None, 0)) == -4
     assert L.ldlt_rpm_factor_batched(*args(3, 7, 1, buf, 1024)) == -4      # less than one CTA's scratch
     assert L.ldlt_rpm_factor_batched(3, None, 7, buf, buf, buf, buf, buf, buf, 1, buf, 1024, None) == -1
-    one = 2 * 512 * 512 * 4
+    one = 512 * 512 * 4
     assert libs.batched_workspace_bytes(1, 65521) == 256 + 256 + one
     assert libs.batched_workspace_bytes(4096, 65521) == 256 + 4096 * 4 + 640 * one
     with pytest.raises(libs.LdltError):

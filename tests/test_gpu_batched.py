@@ -119,8 +119,8 @@ def test_small_workspace_runs_fewer_ctas():
     ns, mats = _mixed_batch(p, 1234, extra=4)
     batch = lr.Batch(ns)
     _fill_host(batch, mats)
-    header = lr.batched_workspace_bytes(len(ns), p) - min(len(ns), 640) * (2 << 20)
-    ws = torch.empty(header + 3 * (2 << 20), dtype=torch.uint8, device="cuda")  # three CTAs
+    header = lr.batched_workspace_bytes(len(ns), p) - min(len(ns), 640) * (1 << 20)
+    ws = torch.empty(header + 3 * (1 << 20), dtype=torch.uint8, device="cuda")  # three CTAs
     lr.factor_batched(batch, p, workspace=ws)
     for i, A in enumerate(mats):
         _assert_oracle(A, p, _out(batch, i))
@@ -174,3 +174,19 @@ def test_config3_batch4096_planted():
         M = Ad.cpu().numpy().astype(np.int64) & 0xFFFFFFFF
         assert np.array_equal(np.tril(M, -1), got["Lstrict"]) and np.array_equal(np.diag(M), got["d"])
         assert np.array_equal(res["perm"].cpu().numpy(), got["perm"])
+
+
+def test_upper_triangle_untouched():
+    p = 65521
+    ns, mats = _mixed_batch(p, 4321, extra=4)
+    batch = lr.Batch(ns)
+    for i, A in enumerate(mats):
+        n = A.shape[0]
+        full = np.tril(A.astype(np.int64)) + np.triu(np.full((n, n), 0x5A5A5A5, dtype=np.int64), 1)
+        batch.matrix(i).copy_(torch.from_numpy(full.astype(np.int32)))
+    lr.factor_batched(batch, p)
+    for i, A in enumerate(mats):
+        n = A.shape[0]
+        M = batch.matrix(i).cpu().numpy().astype(np.int64)
+        assert np.all(np.triu(M, 1) == np.triu(np.full((n, n), 0x5A5A5A5, dtype=np.int64), 1))
+        _assert_oracle(A, p, _out(batch, i))
