@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-schedule line")
     return ap.parse_args()
 
 
@@ -207,6 +208,109 @@ def _host_matrix(name):
     return A
 
 
+def batched_bench(lr, inputs, inputs_gpu, dev, steps):
+    """The batched schedule on the batch workload (4096 planted matrices, n in
+    [32, 512]): one ldlt_rpm_factor_batched call per step, timed with CUDA
+    events around the call (the inputs are restored from a device copy before
+    each step, outside the events); the same call replayed from a captured CUDA
+    graph; and the per-matrix loop of ldlt_rpm_factor on the first 256 matrices,
+    scaled to the batch by effective operations."""
+    import numpy as np
+    import torch
+    name = "batch4096_n32to512_p65521"
+    count, n_lo, n_hi, p = inputs.BATCH_WORKLOADS[name]
+    seed = inputs.SEED_BASE + 3
+    ns, rs = inputs.batch_shapes(count, n_lo, n_hi, seed)
+    batch = lr.Batch(ns, device=dev)
+    partners = inputs_gpu.planted_batch(batch, rs, p, seed)
+    src = batch.arena.clone()
+    ops = float(sum(effective_ops(int(a), int(b)) for a, b in zip(ns, rs)))
+    stream = torch.cuda.current_stream(dev)
+    ws = torch.empty(lr.batched_workspace_bytes(count, p), dtype=torch.uint8, device=dev)
+
+    def run_once():
+        lr.factor_batched(batch, p, workspace=ws, stream=stream, check=False)
+
+    for _ in range(2):
+        batch.arena.copy_(src)
+        run_once()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(steps):
+        batch.arena.copy_(src)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        run_once()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = sum(times) / len(times)
+    ranks = batch.rank[:count].cpu().numpy()
+    status_ok = int((batch.status[:count] != 0).sum().item()) == 0
+    pa = batch.perm_arena.cpu().numpy()
+    perms_ok, off = True, 0
+    for i in range(count):
+        n_i = int(ns[i])
+        pr = partners[i]
+        placed = np.zeros(n_i, dtype=bool)
+        exp, zero = [], []
+        for a in range(n_i):
+            if placed[a]:
+                continue
+            b = pr[a]
+            if b < 0:
+                zero.append(a)
+            elif b == a:
+                exp.append(a); placed[a] = True
+            else:
+                exp += [a, int(b)]; placed[a] = placed[b] = True
+        perms_ok = perms_ok and np.array_equal(pa[off:off + n_i], np.array(exp + zero))
+        off += n_i
+    parity = bool(status_ok and np.array_equal(ranks, rs) and perms_ok)
+
+    graph_ms = None
+    try:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            lr.factor_batched(batch, p, workspace=ws, stream=torch.cuda.current_stream(dev), check=False)
+        gt = []
+        for _ in range(steps):
+            batch.arena.copy_(src)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.replay()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            gt.append(e0.elapsed_time(e1))
+        graph_ms = sum(gt) / len(gt)
+        parity = parity and bool(np.array_equal(batch.rank[:count].cpu().numpy(), rs))
+        del g
+    except Exception as ex:  # capture unsupported in this environment
+        graph_ms = {"unavailable": str(ex)[:200]}
+
+    # per-matrix launch loop (the single-matrix entry point), bounded sample
+    sub = 256
+    batch.arena.copy_(src)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(sub):
+        lr.factor(batch.matrix(i), p, check=False)
+    torch.cuda.synchronize()
+    loop_s = time.perf_counter() - t0
+    ops_sub = float(sum(effective_ops(int(ns[i]), int(rs[i])) for i in range(sub)))
+    loop_est_ms = loop_s * 1e3 * ops / ops_sub
+    del ws, batch, src
+    return {"workload": name, "matrices": count, "p": p, "value": ops / (ms * 1e-3) / 1e9, "unit": UNIT,
+            "ms_per_batch": ms, "graph_ms_per_batch": graph_ms,
+            "effective_ops": ops, "loop_ms_est": loop_est_ms,
+            "loop_sample": "ldlt_rpm_factor on matrices 0..%d, %.1f ms, scaled by effective ops" % (sub - 1, loop_s * 1e3),
+            "speedup_vs_loop": loop_est_ms / ms,
+            "update_form": "mma.sync bf16 2-limb (p < 2^16)",
+            "parity": {"ranks_and_canonical_perms": parity}}
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -365,6 +469,10 @@ def main():
         except lr.LdltError as ex:
             fp64 = {"unavailable": str(ex)}
 
+    batched = None
+    if rank == 0 and not args.no_batched:
+        batched = batched_bench(lr, inputs, inputs_gpu, dev, max(3, min(args.steps, 10)))
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         A_host = np.tril(A0.cpu().numpy()).astype(np.uint32)
@@ -387,6 +495,7 @@ def main():
             "e2e": e2e,
             "gpu_launches": int(round(prof[5])),
             "fp64_form": fp64,
+            "batched": batched,
             "cpu_baseline": cpu}
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -682,7 +682,10 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
         if (tid < np) {
             ring_ready(ev_next);
             za[tid] = zval(tid, sh.U + a, SSTRIDE, sh, f);
-            sh.pend_bw[pt % NPEND][tid] = sh.bw[tid];  // kept only if this row's scan is issued
+            // Snapshot for a rollback to this row, kept only if its scan is issued.
+            // With NPEND scans pending, slot pt % NPEND is still the oldest
+            // scan's snapshot: leave it (this row then waits and is retried).
+            if (pt - ph < NPEND) sh.pend_bw[pt % NPEND][tid] = sh.bw[tid];
         }
         if (tid == 0) {
             sh.dbg[0] += 1;

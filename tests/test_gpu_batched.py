@@ -190,3 +190,25 @@ def test_upper_triangle_untouched():
         M = batch.matrix(i).cpu().numpy().astype(np.int64)
         assert np.all(np.triu(M, 1) == np.triu(np.full((n, n), 0x5A5A5A5, dtype=np.int64), 1))
         _assert_oracle(A, p, _out(batch, i))
+
+
+def test_batched_call_replays_from_a_cuda_graph():
+    """The batched call enqueues a memset and two kernels and reads nothing
+    back, so it can be captured once and replayed."""
+    p = 65521
+    ns, mats = _mixed_batch(p, 2468, extra=6)
+    batch = lr.Batch(ns)
+    _fill_host(batch, mats)
+    src = batch.arena.clone()
+    ws = torch.empty(lr.batched_workspace_bytes(len(ns), p), dtype=torch.uint8, device="cuda")
+    lr.factor_batched(batch, p, workspace=ws)  # warm-up outside the capture
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        lr.factor_batched(batch, p, workspace=ws, stream=torch.cuda.current_stream(), check=False)
+    for _ in range(2):
+        batch.arena.copy_(src)
+        batch.rank.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        for i, A in enumerate(mats):
+            _assert_oracle(A, p, _out(batch, i))

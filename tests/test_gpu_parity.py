@@ -272,6 +272,13 @@ def test_config4_planted_n32768_all_pairs_tc():
     _check_planted_full_size(32768, 16384, True, 2147483647, inputs.SEED_BASE + 4, lr.PATH_TC)
 
 
+def test_planted_n28000_full_scan_fifo():
+    """About 184 far rows per helper CTA: far scans answer slowly, so the
+    leader's FIFO of speculative scans fills up; a scan answered with a
+    partner while the FIFO is full must roll back to its own snapshot."""
+    _check_planted_full_size(28000, 14000, False, 65521, 91 + 28000, lr.PATH_TC)
+
+
 def test_wait_budget_timeout_reports_status():
     """A wait that runs out is reported in the device status word, and the
     context stays usable for the next call."""
