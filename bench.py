@@ -137,8 +137,9 @@ def cpu_oracle_sample(A_host, p, seconds):
 
 
 def profile_traffic(kernel_src):
-    """DRAM traffic per launch of the SYRDK kernel from the committed ncu
-    summary, if it was taken on the current kernel source (else None)."""
+    """DRAM bytes (read + write) of all SYRDK launches of one factorisation of
+    the bench workload, from the committed ncu summary, if it was taken on the
+    current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", "syrdk_tc_n16384.md")
     try:
         txt = open(path).read()
@@ -147,7 +148,7 @@ def profile_traffic(kernel_src):
     src = open(kernel_src, "rb").read()
     h = hashlib.sha256(src).hexdigest()[:16]
     m1 = re.search(r"kernel source sha256\[:16\]:\s*([0-9a-f]{16})", txt)
-    m2 = re.search(r"traffic per full-size launch \(bytes\):\s*([0-9.eE+]+)", txt)
+    m2 = re.search(r"dram bytes per factorisation \(all launches\):\s*([0-9.eE+]+)", txt)
     if not m1 or not m2 or m1.group(1) != h:
         return None
     return float(m2.group(1))

@@ -1,24 +1,47 @@
-"""One factorisation of a planted matrix, for profiling under ncu.
+"""One factorisation (or one batched call) for profiling under ncu.
 
-    python -m paper_1802_10453_gb300.profile_case N [p] [path]
+    python -m paper_1802_10453_gb300.profile_case N [p] [fp64]
+    python -m paper_1802_10453_gb300.profile_case WORKLOAD_NAME
+    python -m paper_1802_10453_gb300.profile_case batch COUNT
 
-Draws A = T R T^T (n = N, rank N/2, a quarter of R's non-zeros in 2x2 pairs)
-on the GPU, factors it once through the C ABI and prints rank and status.
+The first form draws A = T R T^T (n = N, rank N/2, a quarter of R's non-zeros
+in 2x2 pairs, p = 2^26 - 5 unless given) on the GPU; the second draws the named
+workload of inputs.WORKLOADS exactly as bench.py does; both factor it once
+through the C ABI.  The third draws the first COUNT matrices of the batch
+workload (n in [32, 512], p = 65521) and factors them in one batched call.
+Prints rank(s) and status.
 """
 import sys
 
 import torch
 
 import paper_1802_10453_gb300 as lr
-from paper_1802_10453_gb300 import inputs_gpu
+from paper_1802_10453_gb300 import inputs, inputs_gpu
 
 
 def main(argv):
-    n = int(argv[1]) if len(argv) > 1 else 8192
-    p = int(argv[2]) if len(argv) > 2 else 67108859
-    path = lr.PATH_FP64 if (len(argv) > 3 and argv[3] == "fp64") else lr.PATH_TC
-    r = n // 2
-    A, _ = inputs_gpu.planted_matrix(n, r, r // 4, p, 12345)
+    arg = argv[1] if len(argv) > 1 else "8192"
+    if arg == "batch":
+        count = int(argv[2]) if len(argv) > 2 else 1024
+        _, n_lo, n_hi, p = inputs.BATCH_WORKLOADS["batch4096_n32to512_p65521"]
+        seed = inputs.SEED_BASE + 3
+        ns, rs = inputs.batch_shapes(4096, n_lo, n_hi, seed)
+        ns, rs = ns[:count], rs[:count]
+        batch = lr.Batch(ns)
+        inputs_gpu.planted_batch(batch, rs, p, seed)
+        lr.factor_batched(batch, p)
+        ok = bool((batch.rank[:count].cpu() == torch.from_numpy(rs)).all())
+        print("batch", count, "p", p, "ranks as planted", ok)
+        return 0 if ok else 1
+    if arg in inputs.WORKLOADS:
+        A, n, _, p, _ = inputs_gpu.workload_matrix(arg)
+        path = lr.PATH_TC
+    else:
+        n = int(arg)
+        p = int(argv[2]) if len(argv) > 2 else 67108859
+        path = lr.PATH_FP64 if (len(argv) > 3 and argv[3] == "fp64") else lr.PATH_TC
+        r = n // 2
+        A, _ = inputs_gpu.planted_matrix(n, r, r // 4, p, 12345)
     res = lr.factor(A, p, path=path)
     torch.cuda.synchronize()
     print("n", n, "p", p, "rank", int(res["rank"].item()), "status", int(res["status"].item()))
