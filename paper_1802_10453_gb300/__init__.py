@@ -39,3 +39,4 @@ from .binding import (  # noqa: F401
     set_speculation,
     effective_ops,
 )
+from .tune import tune_batched  # noqa: E402,F401

@@ -212,3 +212,20 @@ def test_batched_call_replays_from_a_cuda_graph():
         torch.cuda.synchronize()
         for i, A in enumerate(mats):
             _assert_oracle(A, p, _out(batch, i))
+
+
+def test_autotuner_keeps_results_and_inputs():
+    p = 65521
+    ns, mats = _mixed_batch(p, 1357, extra=8)
+    batch = lr.Batch(ns)
+    _fill_host(batch, mats)
+    before = batch.arena.clone()
+    try:
+        res = lr.tune_batched(batch, p, candidates=((32, 0, 32), (16, 0, 16), (32, 300, 8)), reps=1)
+        assert res["best"] in res["ms"] and all(v > 0 for v in res["ms"].values())
+        assert torch.equal(batch.arena, before)      # the inputs are back in place
+        lr.factor_batched(batch, p)                  # with the chosen schedule
+    finally:
+        lr.set_batched_schedule(32, 0, 32)
+    for i, A in enumerate(mats):
+        _assert_oracle(A, p, _out(batch, i))
