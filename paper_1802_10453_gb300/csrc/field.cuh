@@ -17,6 +17,10 @@ struct FieldP {
     uint32_t inv2;   // (p + 1) / 2, the inverse of 2 for odd p; 0 for p = 2
     uint64_t mu;     // floor((2^64 - 1) / p)
     uint64_t m63;    // multiple of p in (2^62, 2^63]
+    uint32_t c32;    // 2^32 mod p
+    uint32_t c32q;   // floor(c32 * 2^32 / p)   (Shoup companion of c32)
+    uint32_t oneq;   // floor(2^32 / p)         (Shoup companion of 1)
+    uint32_t pad;
 };
 
 inline FieldP make_field(uint32_t p)
@@ -27,6 +31,10 @@ inline FieldP make_field(uint32_t p)
     f.mu = ~0ull / (uint64_t)p;
     uint64_t pp = (uint64_t)p * (uint64_t)p;
     f.m63 = ((1ull << 63) / pp) * pp;  // > 2^62 because pp < 2^62
+    f.c32 = (uint32_t)((1ull << 32) % p);
+    f.c32q = (uint32_t)(((uint64_t)f.c32 << 32) / p);
+    f.oneq = (uint32_t)((1ull << 32) / p);
+    f.pad = 0;
     return f;
 }
 
@@ -37,6 +45,22 @@ __device__ __forceinline__ uint32_t fp_reduce64(uint64_t x, const FieldP &f)
     if (r >= f.p) r -= f.p;
     if (r >= f.p) r -= f.p;
     return (uint32_t)r;
+}
+
+// x mod p for any 64-bit x with 32-bit operations only: x = hi 2^32 + lo with
+// hi * (2^32 mod p) and lo each reduced by Shoup's method (V. Shoup, NTL:
+// multiplication by a fixed w with w' = floor(w 2^32 / p) leaves a remainder
+// in [0, 2p)), then one final correction.  Fewer and cheaper instructions
+// than fp_reduce64 (no 64 x 64-bit high product).
+__device__ __forceinline__ uint32_t fp_reduce64_fold(uint64_t x, const FieldP &f)
+{
+    const uint32_t hi = (uint32_t)(x >> 32), lo = (uint32_t)x;
+    uint32_t a = hi * f.c32 - __umulhi(hi, f.c32q) * f.p;
+    uint32_t b = lo - __umulhi(lo, f.oneq) * f.p;
+    a = a >= f.p ? a - f.p : a;
+    b = b >= f.p ? b - f.p : b;
+    const uint32_t s = a + b;  // < 2p < 2^32
+    return s >= f.p ? s - f.p : s;
 }
 
 __device__ __forceinline__ uint32_t fp_mul(uint32_t a, uint32_t b, const FieldP &f)

@@ -162,6 +162,11 @@ __device__ __forceinline__ void mma_commit(uint32_t bar)
                  : "memory");
 }
 
+__device__ __forceinline__ void cp_async4(uint32_t *dst, const uint32_t *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -356,30 +361,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1) syrdk_tc_kernel(const TcArgs ar
             int I, J;
             tile_of(args.tm, t, I, J);
             // -- gather the old values of this tile (rows wq*32 .. wq*32+31) --
+            // Asynchronous 4-byte copies, all in flight at once: one memory
+            // round trip per tile.  S is only read in this kernel (the new
+            // values go to Snext), so the L1-allocating form sees no stale line.
             {
                 const int j0 = J * BN + lane, j1 = j0 + 32;
                 const int sj0 = j0 < mn ? __ldg(args.sigma + j0) : 0;
                 const int sj1 = j1 < mn ? __ldg(args.sigma + j1) : 0;
                 const int ilane = I * BM + wq * 32 + lane;
                 const int si_lane = ilane < mn ? __ldg(args.sigma + ilane) : 0;
-#pragma unroll
-                for (int r0 = 0; r0 < 32; r0 += 16) {
-                    uint32_t v0[16], v1[16];
-#pragma unroll
-                    for (int r = 0; r < 16; ++r) {
-                        const int i = I * BM + wq * 32 + r0 + r;
-                        const int si = __shfl_sync(0xffffffffu, si_lane, r0 + r);
-                        const uint32_t *srow = args.S + (int64_t)si * args.ldS;
-                        v0[r] = (i < mn && j0 <= i && j0 < mn) ? __ldg(srow + sj0) : 0u;
-                        v1[r] = (i < mn && j1 <= i && j1 < mn) ? __ldg(srow + sj1) : 0u;
-                    }
-#pragma unroll
-                    for (int r = 0; r < 16; ++r) {
-                        const int rr = wq * 32 + r0 + r;
-                        cg[rr * CLD + lane] = v0[r];
-                        cg[rr * CLD + lane + 32] = v1[r];
-                    }
+#pragma unroll 8
+                for (int r = 0; r < 32; ++r) {
+                    const int i = I * BM + wq * 32 + r;
+                    const int si = __shfl_sync(0xffffffffu, si_lane, r);
+                    const uint32_t *srow = args.S + (int64_t)si * args.ldS;
+                    const int rr = wq * 32 + r;
+                    uint32_t *d0 = cg + rr * CLD + lane, *d1 = d0 + 32;
+                    if (i < mn && j0 <= i && j0 < mn) cp_async4(d0, srow + sj0);
+                    else *d0 = 0u;
+                    if (i < mn && j1 <= i && j1 < mn) cp_async4(d1, srow + sj1);
+                    else *d1 = 0u;
                 }
+                asm volatile("cp.async.commit_group;\n" ::: "memory");
+                asm volatile("cp.async.wait_group 0;\n" ::: "memory");
             }
             asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory");
             const uint32_t tph = (tcount >> 1) & 1u;
@@ -408,7 +412,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) syrdk_tc_kernel(const TcArgs ar
                     if (L > 1) v += (int64_t)__float2int_rn(__uint_as_float(r[1][e])) << 8;
                     if (L > 2) v += (int64_t)__float2int_rn(__uint_as_float(r[2][e])) << 16;
                     if (L > 3) v += (int64_t)__float2int_rn(__uint_as_float(r[3][e])) << 24;
-                    o[e] = fp_sub(crow[c0 + e], fp_reduce64((uint64_t)(v + (int64_t)bias), f), f);
+                    o[e] = fp_sub(crow[c0 + e], fp_reduce64_fold((uint64_t)(v + (int64_t)bias), f), f);
                 }
                 const int jb = J * BN + c0;
                 if (i < mn) {
