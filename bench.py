@@ -52,6 +52,24 @@ def dist_env():
     return rank, world, local
 
 
+def tc_digits(p):
+    """Digit counts of the tensor-core update (csrc/syrdk_tc.cu): L_B signed
+    base-256 digits with a top digit of magnitude <= 128 on the B side; on the
+    A side base 512 (digits <= 256, at most 3) when that needs fewer digits."""
+    h = (p - 1) // 2
+
+    def count(base, half, top, lmax):
+        for L in range(1, lmax + 1):
+            low = sum(half * base ** u for u in range(L - 1))
+            if (h + low) // base ** (L - 1) <= top:
+                return L
+        return None
+
+    lb = count(256, 128, 128, 4)
+    la = count(512, 256, 256, min(3, lb - 1)) if lb > 1 else None
+    return lb, (la if la is not None else lb)
+
+
 def effective_ops(n, r):
     n, r = float(n), float(r)
     return r ** 3 / 3.0 + n * n * r - r * r * n
@@ -395,11 +413,11 @@ def main():
 
     # roofline of the dominant kernel (level-3 update on tensor cores)
     pk, pk_kind = peaks()
-    limbs = 4 if p > (1 << 24) else (3 if p > (1 << 16) else 2)
+    limbs_b, limbs_a = tc_digits(p)
     syrdk_ms = prof[2] / args.steps
     macs = prof[3] / args.steps
     launches = prof[4] / args.steps
-    flops_issued_alg = 2.0 * limbs * limbs * macs
+    flops_issued_alg = 2.0 * limbs_a * limbs_b * macs
     achieved = flops_issued_alg / (syrdk_ms * 1e-3) / 1e12 if syrdk_ms > 0 else None
     peak = pk.get("bf16_tflops_sustained", 1700.0)
     traffic = profile_traffic(os.path.join(ROOT, "paper_1802_10453_gb300", "csrc", "syrdk_tc.cu"))
@@ -490,7 +508,7 @@ def main():
             "dtype": "bf16 (8-bit balanced limbs, fp32 accumulate) over u32 residues",
             "data": "synthetic (seeded A = T R T^T, GPU generator)",
             "config": {"workload": args.workload, "n": n, "rank": rank_found, "p": p,
-                       "limbs": limbs, "path": "tcgen05 bf16-limb",
+                       "limbs": {"a_side": limbs_a, "b_side": limbs_b}, "path": "tcgen05 bf16-limb",
                        "l2": "inputs larger than L2 (1 GiB matrix); A restored from a device copy each step (inside the timed region)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "parity": {"rpm_equals_planted": parity},

@@ -122,6 +122,7 @@ cudaError_t launch_syrdk_fp64(const uint32_t *S, int64_t ldS, const int *sigma, 
 
 // Tensor-core form of the level-3 update.
 int tc_limbs(uint32_t p);
+int tc_limbs_a(uint32_t p, int *shift);
 int tc_bn(int limbs);
 size_t tc_operand_bytes(int64_t n, int limbs);
 cudaError_t launch_split_tc(const uint32_t *LpT, int64_t ldL, const int *sigma, int m_next,

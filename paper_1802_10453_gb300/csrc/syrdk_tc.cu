@@ -2,20 +2,23 @@
 //   Z = C - G D G^T   (SYRDK, Section 3), lower triangle, rows compacted.
 //
 // Exact modular products on bf16 tensor cores.  Every residue is written in
-// balanced form (-p/2, p/2] and split into L signed base-256 digits
-// x = sum_u 256^u x_u, x_u in [-128, 128]; such small integers are exact in
-// bf16 and every digit product is at most 2^14 in magnitude.  With
-//   b~_u = balanced(256^u * g mod p)   (pre-scaled copies of the B operand)
+// balanced form (-p/2, p/2] and split into signed digits, small integers that
+// bf16 holds exactly (|d| <= 256).  The A side (G D) uses L_A digits of base
+// beta (256, or 512 when that needs fewer digits: p in (2^24, 2^26]), digits
+// in [-beta/2, beta/2]; the B side uses L_B base-256 digits in [-128, 128].
+// With the pre-scaled copies of the B operand
+//   b~_u = balanced(beta^u * g mod p),   u < L_A,
 // the product sum_k gd_k g_k is congruent mod p to
 //   sum_v 256^v * acc_v,   acc_v = sum_u sum_k digit_u(gd_k) * digit_v(b~_u,k),
-// so each acc_v is ONE matrix product of inner dimension K' = L*K: the A
-// operand is [digit_0(GD) | ... | digit_{L-1}(GD)] and the B operand for acc_v
-// is [digit_v(b~_0) | ... | digit_v(b~_{L-1})].  The L B operands are stacked
-// along N, so a single tcgen05.mma (kind::f16, M = 128, N = L*BN) per K-step
-// produces all acc_v for a 128 x BN output tile.  The FP32 accumulation is
-// exact because |acc_v| <= K' * 2^14 < 2^24 for K' < 1024.  The epilogue reads
-// the L accumulators from tensor memory, forms sum_v 256^v acc_v in 64-bit
-// integers, reduces once mod p and subtracts from the old Schur entry.
+// so each acc_v is ONE matrix product of inner dimension K' = L_A*K: the A
+// operand is [digit_0(GD) | ... | digit_{L_A-1}(GD)] and the B operand for
+// acc_v is [digit_v(b~_0) | ... | digit_v(b~_{L_A-1})].  The L_B B operands are
+// stacked along N, so a single tcgen05.mma (kind::f16, M = 128, N = L_B*BN) per
+// K-step produces all acc_v for a 128 x BN output tile.  The FP32 accumulation
+// is exact: |acc_v| <= K' * (beta/2) * 128 <= 3 * 128 * 2^15 < 2^24 with base
+// 512 (L_A <= 3) and <= 4 * 128 * 2^14 = 2^23 with base 256.  The epilogue
+// reads the L_B accumulators from tensor memory, forms sum_v 256^v acc_v in
+// 64-bit integers, reduces once mod p and subtracts from the old Schur entry.
 //
 // Kernel structure (one CTA per SM, persistent over the lower-triangle tiles):
 //   warp 0      bulk-copy producer (cp.async.bulk, mbarrier complete_tx)
@@ -212,7 +215,7 @@ struct TcArgs {
     int m_next;
     const __nv_bfloat16 *Aop;
     const __nv_bfloat16 *Bop;
-    int limbs, bn, nprime, kprime;  // N' = limbs * bn, K' = limbs * kpad
+    int limbs, bn, nprime, kprime;  // N' = L_B * bn (limbs = L_B), K' = L_A * kpad
     FieldP f;
     uint64_t bias;                  // multiple of p above 2^50
     uint32_t *Snext;
@@ -449,13 +452,14 @@ __device__ __forceinline__ int32_t balanced(uint32_t x, uint32_t p)
     return x > (p >> 1) ? (int32_t)((int64_t)x - (int64_t)p) : (int32_t)x;
 }
 
-// digit u of the balanced base-256 expansion (top digit takes the rest)
-__device__ __forceinline__ void digits(int32_t x, int L, int32_t *d)
+// digit u of the balanced base-2^sh expansion (top digit takes the rest)
+__device__ __forceinline__ void digits(int32_t x, int L, int sh, int32_t *d)
 {
+    const int32_t half = 1 << (sh - 1), mask = (1 << sh) - 1;
     for (int u = 0; u < L - 1; ++u) {
-        int32_t lo = ((x + 128) & 255) - 128;
+        int32_t lo = ((x + half) & mask) - half;
         d[u] = lo;
-        x = (x - lo) >> 8;
+        x = (x - lo) >> sh;
     }
     d[L - 1] = x;
 }
@@ -476,10 +480,10 @@ struct SplitArgs {
     const uint32_t *LpT;
     int64_t ldL;
     const int *sigma;
-    int m_next, np, rows, kpad, limbs, bn, nprime, kprime;
+    int m_next, np, rows, kpad, la, ash, lb, bn, nprime, kprime;  // A: la digits of base 2^ash
     const PanelOut *out;
     FieldP f;
-    uint32_t w256[4];  // 256^u mod p
+    uint32_t wbase[4];  // beta^u mod p
     __nv_bfloat16 *Aop, *Bop;
 };
 
@@ -490,7 +494,7 @@ __global__ void split_tc_kernel(const SplitArgs a)
     const int k0 = blockIdx.y * 8;
     if (i >= a.rows) return;
     const FieldP f = a.f;
-    const int L = a.limbs;
+    const int LA = a.la, LB = a.lb;
     uint32_t g[10];  // g[1 + e] = G[i][k0 + e], e in [-1, 8]
 #pragma unroll
     for (int e = 0; e < 10; ++e) {
@@ -516,8 +520,8 @@ __global__ void split_tc_kernel(const SplitArgs a)
     const int J = i / a.bn, rj = i % a.bn;
     int32_t dg[8][4];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) digits(gd_bal[e], L, dg[e]);
-    for (int u = 0; u < L; ++u) {
+    for (int e = 0; e < 8; ++e) digits(gd_bal[e], LA, a.ash, dg[e]);
+    for (int u = 0; u < LA; ++u) {
         int32_t v8[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) v8[e] = dg[e][u];
@@ -525,17 +529,17 @@ __global__ void split_tc_kernel(const SplitArgs a)
         const int64_t off = (int64_t)I * BM * a.kprime + (int64_t)(kk / 8) * (BM * 8) + ri * 8;
         *(uint4 *)(a.Aop + off) = pack8(v8);
     }
-    // B operand: digit v of b~_u = balanced(256^u g mod p), rows v*bn + rj
+    // B operand: base-256 digit v of b~_u = balanced(beta^u g mod p), rows v*bn + rj
     if (i < ((a.rows + a.bn - 1) / a.bn) * a.bn) {
-        for (int u = 0; u < L; ++u) {
+        for (int u = 0; u < LA; ++u) {
             int32_t db[8][4];
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
-                gb[e] = balanced(fp_mul(a.w256[u], g[e + 1], f), f.p);
-                digits(gb[e], L, db[e]);
+                gb[e] = balanced(fp_mul(a.wbase[u], g[e + 1], f), f.p);
+                digits(gb[e], LB, 8, db[e]);
             }
             const int kk = u * a.kpad + k0;
-            for (int v = 0; v < L; ++v) {
+            for (int v = 0; v < LB; ++v) {
                 int32_t v8[8];
 #pragma unroll
                 for (int e = 0; e < 8; ++e) v8[e] = db[e][v];
@@ -566,6 +570,29 @@ int tc_limbs(uint32_t p)
     return -1;
 }
 
+// Digits of the A side: base 512 when it needs fewer digits than base 256
+// (|digit| <= 256 stays exact in bf16; the accumulation bound above allows
+// L_A <= 3 with base 512), else the base-256 count.  Returns the count and
+// the base's bit width.
+int tc_limbs_a(uint32_t p, int *shift)
+{
+    const int lb = tc_limbs(p);
+    const int64_t h = (int64_t)(p - 1) / 2;
+    for (int L = 1; L <= 3 && L < lb; ++L) {
+        int64_t lowmax = 0, scale = 1;
+        for (int u = 0; u < L - 1; ++u) {
+            lowmax += 256 * scale;
+            scale *= 512;
+        }
+        if ((h + lowmax) / scale <= 256) {
+            *shift = 9;
+            return L;
+        }
+    }
+    *shift = 8;
+    return lb;
+}
+
 int tc_bn(int limbs) { (void)limbs; return BN; }
 
 size_t tc_operand_bytes(int64_t n, int limbs)
@@ -586,13 +613,14 @@ cudaError_t launch_split_tc(const uint32_t *LpT, int64_t ldL, const int *sigma, 
     SplitArgs a;
     a.LpT = LpT; a.ldL = ldL; a.sigma = sigma; a.m_next = m_next; a.np = np;
     a.rows = (int)round_up(m_next, BM);
-    a.kpad = kpad; a.limbs = limbs; a.bn = tc_bn(limbs);
-    a.nprime = limbs * a.bn; a.kprime = limbs * kpad;
+    int ash = 8;
+    a.kpad = kpad; a.lb = limbs; a.la = tc_limbs_a(f.p, &ash); a.ash = ash; a.bn = tc_bn(limbs);
+    a.nprime = limbs * a.bn; a.kprime = a.la * kpad;
     a.out = out; a.f = f;
     uint64_t w = 1;
     for (int u = 0; u < 4; ++u) {
-        a.w256[u] = (uint32_t)(w % f.p);
-        w = (w * 256) % f.p;
+        a.wbase[u] = (uint32_t)(w % f.p);
+        w = (w << ash) % f.p;
     }
     a.Aop = (__nv_bfloat16 *)Aop;
     a.Bop = (__nv_bfloat16 *)Bop;
@@ -609,7 +637,8 @@ cudaError_t launch_syrdk_tc(const uint32_t *S, int64_t ldS, const int *sigma, in
     TcArgs a;
     a.S = S; a.ldS = ldS; a.sigma = sigma; a.m_next = m_next;
     a.Aop = (const __nv_bfloat16 *)Aop; a.Bop = (const __nv_bfloat16 *)Bop;
-    a.limbs = limbs; a.bn = tc_bn(limbs); a.nprime = limbs * a.bn; a.kprime = limbs * kpad;
+    int ash = 8;
+    a.limbs = limbs; a.bn = tc_bn(limbs); a.nprime = limbs * a.bn; a.kprime = tc_limbs_a(f.p, &ash) * kpad;
     a.f = f;
     a.bias = ((((uint64_t)1 << 50) / f.p) + 1) * (uint64_t)f.p;
     a.Snext = Snext; a.budget_ns = budget_ns; a.status = status;
