@@ -288,3 +288,48 @@ def freivalds_check(A, perm, L, d, e, p: int, trials: int = 2, seed: int = 12345
         if not np.array_equal(lhs, rhs):
             return False
     return True
+
+
+def strict_char2(perm, L, d, e, p: int = 2, mistake: str = "none"):
+    """Section 2.2 (Antitriangular decomposition): in characteristic 2 a
+    factorisation with relaxed blocks [[0, c], [c, dd]] (dd != 0) becomes one
+    with only 1x1 and antidiagonal 2x2 blocks, at a cost linear in the size of L.
+
+    Restated for P^T A P = L D L^T with perm, L (rows in perm order), d, e as
+    returned by ldlt_rpm, for every block (k, k+1) with e[k] = c != 0 and
+    d[k+1] = dd != 0:
+      1. the block is invariant under [[1, 0], [l, 1]] congruence mod 2, so
+         L's in-block entry l is folded into column k (column k -= l column k+1);
+      2. [[0, c], [c, dd]] = J [[1, 0], [c/dd, 1]] diag(dd, -c^2/dd) [[1, c/dd], [0, 1]] J,
+         so P becomes P J (positions k, k+1 swap), L becomes (J L J) times
+         [[1, 0], [c/dd, 1]] on columns (k, k+1), and D's block diag(dd, -c^2/dd).
+    Blocks with dd = 0 are already antidiagonal.  For odd p (Algorithm 4 then
+    yields antidiagonal blocks only) nothing changes.  Returns new
+    (perm, L, d, e).  `mistake` plants a known error for the pin tests.
+    """
+    perm = np.array(perm, dtype=np.int64).copy()
+    L = np.array(L, dtype=np.int64).copy() % p
+    d = np.array(d, dtype=np.int64).copy() % p
+    e = np.array(e, dtype=np.int64).copy() % p
+    if p != 2:
+        return perm, L, d, e
+    n = len(perm)
+    blocks = [k for k in range(n - 1) if e[k] != 0 and d[k + 1] != 0]
+    for k in blocks:                                   # step 1
+        ell = L[k + 1, k]
+        L[:, k] = (L[:, k] - ell * L[:, k + 1]) % p
+    for k in blocks:                                   # step 2: J L J and P J
+        if mistake != "no_row_swap":
+            L[[k, k + 1], :] = L[[k + 1, k], :]
+        L[:, [k, k + 1]] = L[:, [k + 1, k]]
+        if mistake != "no_perm_swap":
+            perm[[k, k + 1]] = perm[[k + 1, k]]
+    for k in blocks:                                   # step 2: times [[1, 0], [c/dd, 1]]
+        c, dd = int(e[k]), int(d[k + 1])
+        ratio = c * inv_mod(dd, p) % p
+        if mistake != "no_column_op":
+            L[:, k] = (L[:, k] + ratio * L[:, k + 1]) % p
+        d[k] = dd
+        d[k + 1] = (-c * c * inv_mod(dd, p)) % p
+        e[k] = 0
+    return perm, L, d, e

@@ -336,3 +336,68 @@ def test_planted_mistakes_are_caught(mutation):
             break
     assert caught, mutation
     assert _pins_pass(inputs.planted_matrix(9, 8, 2, 7, 300)[0], 7, "none")
+
+
+# ---- Section 2.2: antitriangular -> strict factorisation in characteristic 2 ----
+def _all_symmetric_f2(n):
+    idx = [(i, j) for i in range(n) for j in range(i + 1)]
+    for bits in range(1 << len(idx)):
+        A = np.zeros((n, n), dtype=np.int64)
+        for q, (i, j) in enumerate(idx):
+            if bits >> q & 1:
+                A[i, j] = A[j, i] = 1
+        yield A
+
+
+def _strict_shape_ok(d, e):
+    # only 1x1 pivots and antidiagonal blocks [[0, c], [c, 0]] remain
+    for k in range(len(d) - 1):
+        if e[k] != 0 and (d[k] != 0 or d[k + 1] != 0):
+            return False
+    return True
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4])
+def test_char2_strict_transform_exhaustive(n):
+    relaxed = 0
+    for A in _all_symmetric_f2(n):
+        f = o.ldlt_rpm(A.astype(np.uint32), 2)
+        if any(f["e"][k] and f["d"][k + 1] for k in range(n - 1)):
+            relaxed += 1
+        perm, L, d, e = o.strict_char2(f["perm"], f["L"], f["d"], f["e"])
+        assert o.check_factor(A, perm, L, d, e, 2)
+        assert np.array_equal(np.triu(L, 1), np.zeros_like(L)) and np.all(np.diag(L) == 1)
+        assert _strict_shape_ok(d, e)
+        assert int(np.count_nonzero(d)) + 2 * int(np.count_nonzero(e)) == f["rank"]
+    assert relaxed > 0 or n < 2  # the relaxed blocks of Section 2.2 do occur
+
+
+def test_char2_strict_worked_example():
+    # [[0, 1], [1, 1]] over F_2: P = I, L = I, D = A; strict form P = J,
+    # L = [[1, 0], [1, 1]], D = diag(1, 1)
+    A = np.array([[0, 1], [1, 1]])
+    f = o.ldlt_rpm(A.astype(np.uint32), 2)
+    assert list(f["perm"]) == [0, 1] and f["e"][0] == 1 and f["d"][1] == 1
+    perm, L, d, e = o.strict_char2(f["perm"], f["L"], f["d"], f["e"])
+    assert list(perm) == [1, 0]
+    assert np.array_equal(L, [[1, 0], [1, 1]])
+    assert list(d) == [1, 1] and list(e) == [0, 0]
+
+
+def test_char2_strict_odd_p_unchanged():
+    A, _, _ = inputs.planted_matrix(40, 30, 8, 7, 3)
+    f = o.ldlt_rpm(A, 7)
+    perm, L, d, e = o.strict_char2(f["perm"], f["L"], f["d"], f["e"], p=7)
+    assert np.array_equal(perm, f["perm"]) and np.array_equal(L, f["L"]) and np.array_equal(e, f["e"])
+
+
+@pytest.mark.parametrize("mistake", ["no_row_swap", "no_perm_swap", "no_column_op"])
+def test_char2_strict_planted_mistakes_fail(mistake):
+    caught = False
+    for A in _all_symmetric_f2(4):
+        f = o.ldlt_rpm(A.astype(np.uint32), 2)
+        perm, L, d, e = o.strict_char2(f["perm"], f["L"], f["d"], f["e"], mistake=mistake)
+        if not o.check_factor(A, perm, L, d, e, 2):
+            caught = True
+            break
+    assert caught
