@@ -110,6 +110,31 @@ int rpm_from_factor(int64_t n, const int32_t *perm, const uint32_t *e,
                     const int64_t *rank, int32_t *rpm_col, void *stream);
 
 /*
+ * ldlt_rpm_strict -- the strict form of a characteristic-2 factorisation
+ * (Section 2.2, "Antitriangular decomposition"), in place on the outputs of
+ * ldlt_rpm_factor / ldlt_rpm_factor_batched for the same A.
+ *
+ * Over F_2 Algorithm 4 may return relaxed blocks [[0, c], [c, d]] with d != 0
+ * (Section 2.2; the only factorisation shape that exists in characteristic
+ * 2).  Each such block is replaced by two 1x1 pivots: its two positions swap
+ * in perm, rows and columns k, k+1 of L are swapped and column k becomes
+ * column k + column k+1 below the block, D's block becomes diag(1, 1) and
+ * e[k] becomes 0.  Afterwards P^T A P = L D L^T still holds with only 1x1
+ * pivots and antidiagonal blocks [[0, c], [c, 0]] in D, but perm and D no
+ * longer reveal the rank profile matrix: call rpm_from_factor before this.
+ *
+ *   n, p, A, lda, perm, e   as passed to / returned by ldlt_rpm_factor (p the
+ *                           same prime).  For odd p nothing changes: the
+ *                           blocks of Algorithm 4 are antidiagonal already.
+ *   stream                  cudaStream_t as void*; three launches are
+ *                           enqueued, nothing is read back.
+ * Returns LDLT_OK, LDLT_ERR_ARG, LDLT_ERR_NOT_PRIME, LDLT_ERR_P_RANGE or
+ * LDLT_ERR_CUDA.
+ */
+int ldlt_rpm_strict(int64_t n, uint32_t p, uint32_t *A, int64_t lda,
+                    int32_t *perm, uint32_t *e, void *stream);
+
+/*
  * ldlt_rpm_factor_batched -- factor `count` independent matrices, each as
  * ldlt_rpm_factor does (same pivot order, same outputs bit for bit), in one
  * persistent launch: the batched use of the method that Section 6 discusses

@@ -35,6 +35,7 @@ from .binding import (  # noqa: F401
     Batch,
     BATCH_MAX_N,
     rpm_from_factor,
+    strict,
     set_wait_budget_ns,
     set_speculation,
     effective_ops,

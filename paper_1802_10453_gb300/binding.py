@@ -33,7 +33,8 @@ NOALLOC_BYTES = 48 << 20
 
 EXPORTS = ["ldlt_rpm_workspace_bytes", "ldlt_rpm_factor", "rpm_from_factor", "ldlt_rpm_version",
            "ldlt_rpm_set_wait_budget_ns", "ldlt_rpm_set_speculation", "ldlt_rpm_factor_noalloc",
-           "ldlt_rpm_factor_batched", "ldlt_rpm_batched_workspace_bytes", "ldlt_rpm_batched_set_schedule"]
+           "ldlt_rpm_factor_batched", "ldlt_rpm_batched_workspace_bytes", "ldlt_rpm_batched_set_schedule",
+           "ldlt_rpm_strict"]
 BATCH_MAX_N = 512  # LDLT_BATCH_MAX_N
 
 
@@ -76,6 +77,8 @@ def lib():
             L.ldlt_rpm_batched_workspace_bytes.argtypes = [c_i64, c_u32, ctypes.c_int, ctypes.POINTER(c_sz)]
             L.ldlt_rpm_batched_set_schedule.restype = ctypes.c_int
             L.ldlt_rpm_batched_set_schedule.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+            L.ldlt_rpm_strict.restype = ctypes.c_int
+            L.ldlt_rpm_strict.argtypes = [c_i64, c_u32, c_vp, c_i64, c_vp, c_vp, c_vp]
             L.rpm_from_factor.restype = ctypes.c_int
             L.rpm_from_factor.argtypes = [c_i64, c_vp, c_vp, c_vp, c_vp, c_vp]
             L.ldlt_rpm_version.restype = ctypes.c_int
@@ -295,6 +298,22 @@ def factor_batched(batch: "Batch", p: int, path: int = PATH_TC, stream=None, wor
             i = int(bad[0, 0])
             raise LdltError(int(batch.status[i].item()), "matrix %d of the batch" % i)
     return batch.status
+
+
+def strict(A, res: dict, stream=None) -> dict:
+    """ldlt_rpm_strict on the output of factor() for the same A (in place):
+    characteristic 2 relaxed blocks become 1x1 pivots (Section 2.2); a no-op
+    for odd p.  Take the rank profile matrix (rpm_from_factor) before this."""
+    import torch
+    n = res["n"]
+    if stream is None:
+        stream = torch.cuda.current_stream(A.device)
+    lda = A.stride(0) if n > 0 else 1
+    rc = lib().ldlt_rpm_strict(n, int(res["p"]), A.data_ptr(), lda, res["perm"].data_ptr(), res["e"].data_ptr(),
+                               stream.cuda_stream)
+    if rc != LDLT_OK:
+        raise LdltError(rc, "ldlt_rpm_strict")
+    return res
 
 
 def rpm_from_factor(res: dict, stream=None):

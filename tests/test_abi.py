@@ -122,3 +122,14 @@ def test_batched_host_checks(libs):
     for bad in [(8, 0, 8), (32, -1, 32), (32, 514, 32), (32, 0, 3), (16, 0, 32)]:
         assert L.ldlt_rpm_batched_set_schedule(*bad) == -1
     assert L.ldlt_rpm_batched_set_schedule(32, 0, 32) == 0
+
+
+def test_strict_host_checks(libs):
+    L = libs.lib()
+    buf = ctypes.create_string_buffer(64)
+    assert L.ldlt_rpm_strict(4, 15, buf, 4, buf, buf, None) == -2
+    assert L.ldlt_rpm_strict(-1, 2, buf, 4, buf, buf, None) == -1
+    assert L.ldlt_rpm_strict(4, 2, buf, 3, buf, buf, None) == -1
+    assert L.ldlt_rpm_strict(4, 2, None, 4, buf, buf, None) == -1
+    assert L.ldlt_rpm_strict(4, 7, buf, 4, buf, buf, None) == 0   # odd p: nothing to do, no device work
+    assert L.ldlt_rpm_strict(0, 2, None, 1, None, None, None) == 0

@@ -294,3 +294,44 @@ def test_wait_budget_timeout_reports_status():
         lr.set_wait_budget_ns(0)
     assert st in (0, lr.LDLT_ERR_TIMEOUT)
     assert_parity(A, p, lr.PATH_TC)
+
+
+@pytest.mark.parametrize("n,kind", [(2, "worked"), (5, "uniform"), (64, "planted"), (300, "planted"),
+                                    (513, "uniform"), (700, "planted")])
+def test_char2_strict_transform(n, kind):
+    """Section 2.2: the strict characteristic-2 form on the GPU equals the
+    oracle's transform of the oracle's factorisation, bit for bit, and is a
+    factorisation with 1x1 and antidiagonal blocks only."""
+    p = 2
+    if kind == "worked":
+        A = np.array([[0, 1], [1, 1]], dtype=np.uint32)
+    elif kind == "uniform":
+        A = inputs.uniform_symmetric(n, p, 17 + n)
+    else:
+        A, _, _ = inputs.planted_matrix(n, (3 * n) // 4, n // 4, p, 19 + n)
+    Ad = torch.from_numpy(np.tril(A.astype(np.int64)).astype(np.int32)).cuda()
+    res = lr.factor(Ad, p)
+    lr.strict(Ad, res)
+    torch.cuda.synchronize()
+    out = Ad.cpu().numpy().astype(np.int64) & 0xFFFFFFFF
+    ref = o.ldlt_rpm(A, p)
+    perm, L, d, e = o.strict_char2(ref["perm"], ref["L"], ref["d"], ref["e"])
+    assert np.array_equal(res["perm"].cpu().numpy().astype(np.int64), perm)
+    assert np.array_equal(np.diag(out), d)
+    assert np.array_equal(res["e"].cpu().numpy().astype(np.int64) & 0xFFFFFFFF, e)
+    assert np.array_equal(np.tril(out, -1), np.tril(L, -1))
+    Lg = np.tril(out, -1)
+    Lg[np.arange(n), np.arange(n)] = 1
+    assert o.check_factor(A, perm, Lg, d, e, p)
+    for k in range(n - 1):  # only 1x1 pivots and antidiagonal blocks remain
+        assert e[k] == 0 or (d[k] == 0 and d[k + 1] == 0)
+
+
+def test_strict_is_a_noop_for_odd_p():
+    A, _, _ = inputs.planted_matrix(300, 200, 50, 65521, 23)
+    Ad = torch.from_numpy(np.tril(A.astype(np.int64)).astype(np.int32)).cuda()
+    res = lr.factor(Ad, 65521)
+    before = (Ad.clone(), res["perm"].clone(), res["e"].clone())
+    lr.strict(Ad, res)
+    torch.cuda.synchronize()
+    assert torch.equal(Ad, before[0]) and torch.equal(res["perm"], before[1]) and torch.equal(res["e"], before[2])
