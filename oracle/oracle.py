@@ -333,3 +333,52 @@ def strict_char2(perm, L, d, e, p: int = 2, mistake: str = "none"):
         d[k + 1] = (-c * c * inv_mod(dd, p)) % p
         e[k] = 0
     return perm, L, d, e
+
+
+def solve_factor(perm, L, d, e, rank: int, B, p: int):
+    """A X = B from P^T A P = L D L^T (abstract; the motivation of Section 1:
+    solving symmetric systems with the factorisation), one step at a time:
+      Y = P^T B;  L Z = Y (unit lower triangular, forward);  D W = Z (1x1
+      pivots d_k; 2x2 blocks [[0, x], [x, y]]: w1 = z0 / x, w0 = (z1 - y w1) / x;
+      rows k >= rank: the system is consistent only if z_k = 0, and w_k = 0);
+      L^T V = W (backward);  X = P V.
+    Returns (X, consistent).  X is the solution with zero components on the
+    non-pivot rows (unique when rank = n)."""
+    perm = np.asarray(perm, dtype=np.int64)
+    Lm = np.asarray(L, dtype=np.int64) % p
+    d = np.asarray(d, dtype=np.int64) % p
+    e = np.asarray(e, dtype=np.int64) % p
+    B = np.asarray(B, dtype=np.int64) % p
+    if B.ndim == 1:
+        B = B[:, None]
+    n = len(perm)
+    Y = B[perm].copy()
+    Z = Y.copy()
+    for k in range(n):                      # forward, unit diagonal
+        if k:
+            Z[k] = (Y[k] - matmul_mod(Lm[k:k + 1, :k], Z[:k], p)[0]) % p
+    W = np.zeros_like(Z)
+    consistent = True
+    k = 0
+    while k < n:
+        if k >= rank:
+            if np.any(Z[k] != 0):
+                consistent = False
+            W[k] = 0
+            k += 1
+        elif e[k] != 0:
+            x, y = int(e[k]), int(d[k + 1])
+            ix = inv_mod(x, p)
+            W[k + 1] = (Z[k] * ix) % p
+            W[k] = ((Z[k + 1] - (y * W[k + 1]) % p) % p * ix) % p
+            k += 2
+        else:
+            W[k] = (Z[k] * inv_mod(int(d[k]), p)) % p
+            k += 1
+    V = W.copy()
+    for k in range(n - 1, -1, -1):          # backward with L^T
+        if k < n - 1:
+            V[k] = (W[k] - matmul_mod(Lm[k + 1:, k][None, :], V[k + 1:], p)[0]) % p
+    X = np.zeros_like(V)
+    X[perm] = V
+    return X, consistent

@@ -401,3 +401,59 @@ def test_char2_strict_planted_mistakes_fail(mistake):
             caught = True
             break
     assert caught
+
+
+# ---- consumer: A X = B from the factorisation ----
+@pytest.mark.parametrize("p", [2, 3, 65521, 2147483647])
+def test_solve_full_rank_is_exact(p):
+    rng = np.random.default_rng(p % 1000)
+    for n in (1, 2, 7, 40):
+        A, _, _ = inputs.planted_matrix(n, n, n // 4, p, 100 + n)
+        f = o.ldlt_rpm(A, p)
+        assert f["rank"] == n
+        B = rng.integers(0, p, size=(n, 3), dtype=np.int64)
+        X, ok = o.solve_factor(f["perm"], f["L"], f["d"], f["e"], f["rank"], B, p)
+        assert ok
+        S = o.symmetrize_lower(A, p)
+        assert np.array_equal(o.matmul_mod(S, X, p), B % p)
+        # unique solution: agrees with Gaussian elimination's answer on one column
+        Ainv_b = _gauss_solve(S, B[:, 0], p)
+        assert np.array_equal(X[:, 0], Ainv_b)
+
+
+def _gauss_solve(S, b, p):
+    """Plain Gauss-Jordan elimination mod p for a non-singular S (textbook)."""
+    n = S.shape[0]
+    M = np.concatenate([S % p, (b % p)[:, None]], axis=1).astype(object)
+    for c in range(n):
+        piv = next(i for i in range(c, n) if M[i, c] % p)
+        M[[c, piv]] = M[[piv, c]]
+        M[c] = (M[c] * o.inv_mod(int(M[c, c]), p)) % p
+        for i in range(n):
+            if i != c and M[i, c] % p:
+                M[i] = (M[i] - M[i, c] * M[c]) % p
+    return np.array([int(v) for v in M[:, n]], dtype=np.int64)
+
+
+@pytest.mark.parametrize("p", [2, 7, 65521])
+def test_solve_singular_consistency(p):
+    rng = np.random.default_rng(7 + p)
+    n, r = 30, 18
+    A, _, _ = inputs.planted_matrix(n, r, r // 4, p, 55)
+    S = o.symmetrize_lower(A, p)
+    f = o.ldlt_rpm(A, p)
+    assert f["rank"] == r
+    # B in the column space: B = S Y for a random Y
+    Yr = rng.integers(0, p, size=(n, 2), dtype=np.int64)
+    B = o.matmul_mod(S, Yr, p)
+    X, ok = o.solve_factor(f["perm"], f["L"], f["d"], f["e"], f["rank"], B, p)
+    assert ok and np.array_equal(o.matmul_mod(S, X, p), B)
+    # a right-hand side outside the column space is reported
+    found = False
+    for trial in range(20):
+        b = rng.integers(0, p, size=n, dtype=np.int64)
+        _, ok = o.solve_factor(f["perm"], f["L"], f["d"], f["e"], f["rank"], b, p)
+        in_space = o.rank_mod_p(np.concatenate([S, b[:, None]], axis=1), p) == r
+        assert ok == in_space
+        found = found or not ok
+    assert found
