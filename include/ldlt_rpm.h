@@ -42,6 +42,7 @@ extern "C" {
 #define LDLT_ERR_TIMEOUT    -6  /* device only: a bounded spin-wait gave up        */
 #define LDLT_ERR_NO_DEVICE  -7  /* no sm_103 device visible                         */
 #define LDLT_ERR_TOO_LARGE  -8  /* n above LDLT_NOALLOC_MAX_N (no-allocation entry) */
+#define LDLT_ERR_INCONSISTENT -9 /* device only (ldlt_rpm_solve): B not in A's column space */
 
 /* ---- arithmetic paths for the level-3 updates (SYRDK, Algorithm 2) ------ */
 /* FP64 form: residues carried in doubles, products accumulated with one
@@ -108,6 +109,35 @@ int ldlt_rpm_factor(int64_t n, uint32_t p, uint32_t *A, int64_t lda,
  */
 int rpm_from_factor(int64_t n, const int32_t *perm, const uint32_t *e,
                     const int64_t *rank, int32_t *rpm_col, void *stream);
+
+/*
+ * ldlt_rpm_solve -- A X = B with the factorisation of A (Section 1: a
+ * symmetric triangular factorisation is the kernel for solving symmetric
+ * systems).  From P^T A P = L D L^T:  Z = P^T B, L Z' = Z, D W = Z',
+ * L^T V = W, X = P V.  On the rows k >= rank the system is consistent only if
+ * Z'_k = 0; X is then the solution whose non-pivot components (in pivot
+ * order) are 0, the unique one when rank = n.
+ *
+ *   n, p, A, lda, perm, e, rank   the outputs of ldlt_rpm_factor for A (A as
+ *                                 overwritten by it; rank read on the device).
+ *   B        n x nrhs row-major uint32 (device), leading dimension ldb >= nrhs;
+ *            entries are reduced mod p.  Not modified.
+ *   X        n x nrhs row-major uint32 output (device), ldx >= nrhs; may not
+ *            alias B.
+ *   status   int32[1] (device): 0, or LDLT_ERR_INCONSISTENT when B has a
+ *            column outside A's column space (X is then unspecified).
+ *   ws       device workspace of at least 4 * n * nrhs bytes.
+ *   stream   cudaStream_t as void*; about 4 n / 64 kernels are enqueued (one
+ *            diagonal-block solve and one update per block of 64 rows, both
+ *            directions); nothing is read back.
+ * Returns LDLT_OK, LDLT_ERR_ARG, LDLT_ERR_NOT_PRIME, LDLT_ERR_P_RANGE,
+ * LDLT_ERR_WORKSPACE or LDLT_ERR_CUDA.
+ */
+int ldlt_rpm_solve(int64_t n, uint32_t p, const uint32_t *A, int64_t lda,
+                   const int32_t *perm, const uint32_t *e, const int64_t *rank,
+                   const uint32_t *B, int64_t ldb, int64_t nrhs,
+                   uint32_t *X, int64_t ldx, int32_t *status,
+                   void *ws, size_t ws_bytes, void *stream);
 
 /*
  * ldlt_rpm_strict -- the strict form of a characteristic-2 factorisation

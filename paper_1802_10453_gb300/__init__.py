@@ -36,6 +36,8 @@ from .binding import (  # noqa: F401
     BATCH_MAX_N,
     rpm_from_factor,
     strict,
+    solve,
+    LDLT_ERR_INCONSISTENT,
     set_wait_budget_ns,
     set_speculation,
     effective_ops,

@@ -24,9 +24,10 @@ LDLT_ERR_CUDA = -5
 LDLT_ERR_TIMEOUT = -6
 LDLT_ERR_NO_DEVICE = -7
 LDLT_ERR_TOO_LARGE = -8
+LDLT_ERR_INCONSISTENT = -9
 _NAMES = {0: "LDLT_OK", -1: "LDLT_ERR_ARG", -2: "LDLT_ERR_NOT_PRIME", -3: "LDLT_ERR_P_RANGE",
           -4: "LDLT_ERR_WORKSPACE", -5: "LDLT_ERR_CUDA", -6: "LDLT_ERR_TIMEOUT",
-          -7: "LDLT_ERR_NO_DEVICE", -8: "LDLT_ERR_TOO_LARGE"}
+          -7: "LDLT_ERR_NO_DEVICE", -8: "LDLT_ERR_TOO_LARGE", -9: "LDLT_ERR_INCONSISTENT"}
 # largest order and scratch size of ldlt_rpm_factor_noalloc (LDLT_NOALLOC_* in the header)
 NOALLOC_MAX_N = 1024
 NOALLOC_BYTES = 48 << 20
@@ -34,7 +35,7 @@ NOALLOC_BYTES = 48 << 20
 EXPORTS = ["ldlt_rpm_workspace_bytes", "ldlt_rpm_factor", "rpm_from_factor", "ldlt_rpm_version",
            "ldlt_rpm_set_wait_budget_ns", "ldlt_rpm_set_speculation", "ldlt_rpm_factor_noalloc",
            "ldlt_rpm_factor_batched", "ldlt_rpm_batched_workspace_bytes", "ldlt_rpm_batched_set_schedule",
-           "ldlt_rpm_strict"]
+           "ldlt_rpm_strict", "ldlt_rpm_solve"]
 BATCH_MAX_N = 512  # LDLT_BATCH_MAX_N
 
 
@@ -77,6 +78,9 @@ def lib():
             L.ldlt_rpm_batched_workspace_bytes.argtypes = [c_i64, c_u32, ctypes.c_int, ctypes.POINTER(c_sz)]
             L.ldlt_rpm_batched_set_schedule.restype = ctypes.c_int
             L.ldlt_rpm_batched_set_schedule.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+            L.ldlt_rpm_solve.restype = ctypes.c_int
+            L.ldlt_rpm_solve.argtypes = [c_i64, c_u32, c_vp, c_i64, c_vp, c_vp, c_vp, c_vp, c_i64, c_i64, c_vp,
+                                         c_i64, c_vp, c_vp, c_sz, c_vp]
             L.ldlt_rpm_strict.restype = ctypes.c_int
             L.ldlt_rpm_strict.argtypes = [c_i64, c_u32, c_vp, c_i64, c_vp, c_vp, c_vp]
             L.rpm_from_factor.restype = ctypes.c_int
@@ -298,6 +302,38 @@ def factor_batched(batch: "Batch", p: int, path: int = PATH_TC, stream=None, wor
             i = int(bad[0, 0])
             raise LdltError(int(batch.status[i].item()), "matrix %d of the batch" % i)
     return batch.status
+
+
+def solve(A, res: dict, B, stream=None, workspace=None, check: bool = True):
+    """ldlt_rpm_solve: X with A_orig X = B, from the factor res = factor(A_orig)
+    (A is the factored matrix in place).  B: CUDA int32 tensor (n,) or
+    (n, nrhs).  Returns (X, status tensor); with check=True raises
+    LdltError(LDLT_ERR_INCONSISTENT) when B is outside A's column space."""
+    import torch
+    n = res["n"]
+    B2 = B.reshape(n, -1) if B.dim() == 1 else B
+    if B2.stride(1) != 1 or B2.dtype != torch.int32 or not B2.is_cuda:
+        raise LdltError(LDLT_ERR_ARG, "B must be a CUDA int32 tensor with contiguous rows")
+    nrhs = B2.shape[1]
+    X = torch.empty((n, nrhs), dtype=torch.int32, device=B2.device)
+    status = torch.zeros(1, dtype=torch.int32, device=B2.device)
+    if workspace is None:
+        workspace = torch.empty(max(4 * n * nrhs, 256), dtype=torch.uint8, device=B2.device)
+    if stream is None:
+        stream = torch.cuda.current_stream(B2.device)
+    lda = A.stride(0) if n > 0 else 1
+    rc = lib().ldlt_rpm_solve(n, int(res["p"]), A.data_ptr(), lda, res["perm"].data_ptr(), res["e"].data_ptr(),
+                              res["rank"].data_ptr(), B2.data_ptr(), B2.stride(0) if n else max(nrhs, 1), nrhs,
+                              X.data_ptr(), max(nrhs, 1), status.data_ptr(), workspace.data_ptr(),
+                              workspace.numel(), stream.cuda_stream)
+    if rc != LDLT_OK:
+        raise LdltError(rc, "ldlt_rpm_solve")
+    if check:
+        stream.synchronize()
+        st = int(status.item())
+        if st != 0:
+            raise LdltError(st, "ldlt_rpm_solve")
+    return (X.reshape(-1) if B.dim() == 1 else X), status
 
 
 def strict(A, res: dict, stream=None) -> dict:

@@ -133,3 +133,12 @@ def test_strict_host_checks(libs):
     assert L.ldlt_rpm_strict(4, 2, None, 4, buf, buf, None) == -1
     assert L.ldlt_rpm_strict(4, 7, buf, 4, buf, buf, None) == 0   # odd p: nothing to do, no device work
     assert L.ldlt_rpm_strict(0, 2, None, 1, None, None, None) == 0
+
+
+def test_solve_host_checks(libs):
+    L = libs.lib()
+    buf = ctypes.create_string_buffer(256)
+    args = lambda n, p, lda, ldb, nrhs, ldx, ws, nb: (n, p, buf, lda, buf, buf, buf, buf, ldb, nrhs, buf, ldx, buf, ws, nb, None)
+    assert L.ldlt_rpm_solve(*args(4, 15, 4, 1, 1, 1, buf, 256)) == -2
+    assert L.ldlt_rpm_solve(*args(-1, 7, 4, 1, 1, 1, buf, 256)) == -1
+    assert L.ldlt_rpm_solve(4, 7, buf, 4, buf, buf, buf, buf, 1, 1, buf, 1, None, buf, 256, None) == -1  # status NULL
