@@ -492,6 +492,29 @@ def main():
         except lr.LdltError as ex:
             fp64 = {"unavailable": str(ex)}
 
+    # consumer: A X = B with the factor of the timed step (n = 16384)
+    solve_line = None
+    if rank == 0:
+        sv = {}
+        for nrhs in (1, 64):
+            Bd = torch.randint(0, p, (n, nrhs), dtype=torch.int32, device=dev)
+            wsv = torch.empty(4 * n * nrhs, dtype=torch.uint8, device=dev)
+            lr.solve(A, res, Bd, workspace=wsv, check=False)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(3):
+                lr.solve(A, res, Bd, workspace=wsv, check=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_sv = e0.elapsed_time(e1) / 3
+            # L is read once forward and once backward: 2 * 4 * n(n-1)/2 bytes
+            gbs = 4.0 * n * (n - 1) / (ms_sv * 1e-3) / 1e9
+            sv[str(nrhs)] = {"ms": ms_sv, "L_read_GBps": gbs}
+        solve_line = {"n": n, "by_nrhs": sv, "form": "blocked forward/backward substitution, 64-row blocks",
+                      "note": "random B (consistency not required for timing)"}
+
     batched = None
     if rank == 0 and not args.no_batched:
         batched = batched_bench(lr, inputs, inputs_gpu, dev, max(3, min(args.steps, 10)))
@@ -519,6 +542,7 @@ def main():
             "gpu_launches": int(round(prof[5])),
             "fp64_form": fp64,
             "batched": batched,
+            "solve": solve_line,
             "cpu_baseline": cpu}
     if rank == 0:
         print(json.dumps(line), flush=True)
