@@ -9,9 +9,10 @@
 //   L^T V = W                       backward substitution
 //   X = P V                         scatter rows
 // The triangular solves run in blocks of SB rows: one CTA solves the diagonal
-// block (one thread per right-hand-side column, sequential over the block's
-// rows), then every remaining row takes the block's contribution (one thread
-// per (row, column), SB multiply-adds with one reduction).  Bounded work, no
+// block (staged in shared memory; one warp per right-hand-side column, the
+// block's rows in sequence, each row's dot split over the lanes), then every
+// remaining row takes the block's contribution (one thread per (row, column),
+// SB multiply-adds with one reduction).  Bounded work, no
 // inter-CTA waits; block steps are ordered by the stream.
 #include <cstdint>
 
@@ -32,17 +33,49 @@ __global__ void sv_gather_kernel(int64_t n, int64_t nrhs, const int32_t *perm, c
     Z[idx] = v >= f.p ? v % f.p : v;
 }
 
-// rows [b0, b1): Z[i] -= sum_{b0 <= j < i} L[i][j] Z[j], one column per thread
+// The diagonal block of L (rows and columns [b0, b1)) staged in shared memory
+// (row stride SB + 1: conflict-free column reads for the transposed solve).
+__device__ __forceinline__ void sv_stage_block(uint32_t (*Lb)[SB + 1], int64_t b0, int nb, const uint32_t *A,
+                                               int64_t lda)
+{
+    for (int q = threadIdx.x; q < SB * SB; q += blockDim.x) {
+        const int r = q / SB, c = q % SB;
+        Lb[r][c] = (r < nb && c < nb) ? A[(b0 + r) * lda + b0 + c] : 0u;
+    }
+    __syncthreads();
+}
+
+// sum over the warp of per-lane residues, mod p (every lane gets the result)
+__device__ __forceinline__ uint32_t sv_warp_sum(uint32_t v, const FieldP &f)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fp_add(v, __shfl_xor_sync(0xffffffffu, v, o), f);
+    return v;
+}
+
+// rows [b0, b1): Z[i] -= sum_{b0 <= j < i} L[i][j] Z[j].  One warp per
+// right-hand-side column: lane l holds rows b0 + l and b0 + 32 + l; the dot of
+// row i is split over the lanes and summed by shuffles.
 __global__ void sv_fwd_diag_kernel(int64_t b0, int64_t b1, const uint32_t *A, int64_t lda, uint32_t *Z,
                                    int64_t nrhs, FieldP f)
 {
-    for (int64_t c = threadIdx.x; c < nrhs; c += blockDim.x) {
-        for (int64_t i = b0 + 1; i < b1; ++i) {
-            const uint32_t *Li = A + i * lda;
+    __shared__ uint32_t Lb[SB][SB + 1];
+    const int nb = (int)(b1 - b0);
+    sv_stage_block(Lb, b0, nb, A, lda);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int64_t c = warp; c < nrhs; c += nw) {
+        uint32_t z0 = lane < nb ? Z[(b0 + lane) * nrhs + c] : 0u;
+        uint32_t z1 = lane + 32 < nb ? Z[(b0 + 32 + lane) * nrhs + c] : 0u;
+        for (int i = 1; i < nb; ++i) {
             uint64_t acc = 0;
-            for (int64_t j = b0; j < i; ++j) fp_mac(acc, Li[j], Z[j * nrhs + c], f);
-            Z[i * nrhs + c] = fp_sub(Z[i * nrhs + c], fp_reduce64(acc, f), f);
+            if (lane < i) fp_mac(acc, Lb[i][lane], z0, f);
+            if (lane + 32 < i) fp_mac(acc, Lb[i][lane + 32], z1, f);
+            const uint32_t s = sv_warp_sum(fp_reduce64(acc, f), f);
+            if (i == lane) z0 = fp_sub(z0, s, f);
+            if (i == lane + 32) z1 = fp_sub(z1, s, f);
         }
+        if (lane < nb) Z[(b0 + lane) * nrhs + c] = z0;
+        if (lane + 32 < nb) Z[(b0 + 32 + lane) * nrhs + c] = z1;
     }
 }
 
@@ -86,16 +119,27 @@ __global__ void sv_dsolve_kernel(int64_t n, const uint32_t *A, int64_t lda, cons
     }
 }
 
-// rows [b0, b1) from the last: Z[i] -= sum_{i < j < b1} L[j][i] Z[j]
+// rows [b0, b1) from the last: Z[i] -= sum_{i < j < b1} L[j][i] Z[j] (warp per column)
 __global__ void sv_bwd_diag_kernel(int64_t b0, int64_t b1, const uint32_t *A, int64_t lda, uint32_t *Z,
                                    int64_t nrhs, FieldP f)
 {
-    for (int64_t c = threadIdx.x; c < nrhs; c += blockDim.x) {
-        for (int64_t i = b1 - 2; i >= b0; --i) {
+    __shared__ uint32_t Lb[SB][SB + 1];
+    const int nb = (int)(b1 - b0);
+    sv_stage_block(Lb, b0, nb, A, lda);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int64_t c = warp; c < nrhs; c += nw) {
+        uint32_t z0 = lane < nb ? Z[(b0 + lane) * nrhs + c] : 0u;
+        uint32_t z1 = lane + 32 < nb ? Z[(b0 + 32 + lane) * nrhs + c] : 0u;
+        for (int i = nb - 2; i >= 0; --i) {
             uint64_t acc = 0;
-            for (int64_t j = i + 1; j < b1; ++j) fp_mac(acc, A[j * lda + i], Z[j * nrhs + c], f);
-            Z[i * nrhs + c] = fp_sub(Z[i * nrhs + c], fp_reduce64(acc, f), f);
+            if (lane > i && lane < nb) fp_mac(acc, Lb[lane][i], z0, f);
+            if (lane + 32 > i && lane + 32 < nb) fp_mac(acc, Lb[lane + 32][i], z1, f);
+            const uint32_t s = sv_warp_sum(fp_reduce64(acc, f), f);
+            if (i == lane) z0 = fp_sub(z0, s, f);
+            if (i == lane + 32) z1 = fp_sub(z1, s, f);
         }
+        if (lane < nb) Z[(b0 + lane) * nrhs + c] = z0;
+        if (lane + 32 < nb) Z[(b0 + 32 + lane) * nrhs + c] = z1;
     }
 }
 
