@@ -157,6 +157,15 @@ struct Shared {
     long long dbg[16];                 // diagnostics (thread-0 / lane-0 owned slots)
 };
 
+// load with acquire semantics at GPU scope: later reads of this thread see
+// every write that was made visible before the matching release / fence
+__device__ __forceinline__ int ld_acquire(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
 __device__ void raise_timeout(const PanelParams &P)
 {
     atomicExch(P.status, LDLT_ERR_TIMEOUT_CODE);
@@ -237,10 +246,9 @@ __device__ void helper_cta(const PanelParams &P, Shared &sh, int lo, int hi)
             int avail = 0;
             if (lane == 0) {
                 Spin sp;
-                volatile int *cnt = &P.sync->ev_count;
                 volatile int *ab = &P.sync->abort;
                 for (;;) {
-                    const int c = *cnt;
+                    const int c = ld_acquire(&P.sync->ev_count);
                     const int room = sh.ev_done + NSLOT;
                     const int lim = c < room ? c : room;
                     if (lim > e) { avail = lim - e; break; }
@@ -253,7 +261,7 @@ __device__ void helper_cta(const PanelParams &P, Shared &sh, int lo, int hi)
                 if (lane == 0) { __threadfence_block(); sh.quit = 1; }
                 return;
             }
-            __threadfence();
+            __syncwarp();  // lane 0's acquire of the count orders the record reads of the warp
             bool end = false;
             for (int q = 0; q < avail; ++q) {
                 // one round trip: header and the first 2*KP_MAX payload words
@@ -542,17 +550,15 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
                 }
                 if (go) {
                     go = 0;
-                    volatile int *done = &P.scans[id].done;
                     volatile int *ab = &P.sync->abort;
                     Spin sp2;
                     for (;;) {
-                        if (*done >= nh) { go = 1; break; }
+                        if (ld_acquire(&P.scans[id].done) >= nh) { go = 1; break; }
                         if (*ab || sh.quit) break;
                         if (sp2.expired(P.budget_ns)) { raise_timeout(P); break; }
                     }
                     if (go) {
-                        __threadfence();
-                        v = __ldcg(&P.scans[id].min);
+                        v = __ldcg(&P.scans[id].min);  // ordered after the acquire above
                         sh.res_min[id % SRING] = v;
                         __threadfence_block();
                         sh.scan_resolved = id + 1;
