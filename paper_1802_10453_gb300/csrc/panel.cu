@@ -111,6 +111,12 @@ __device__ __forceinline__ void mac(uint64_t &acc, uint32_t a, uint32_t b, const
 }
 
 constexpr int NPEND = 16;                     // speculative far scans in flight
+// The far-scan bookkeeping (issue, answers, rollback requests) runs on one
+// thread of the last compute warp, which holds no z entry (np <= KP_MAX < CTL),
+// so it overlaps the z vector of the first warps.  It alone writes the pend_*
+// records between barriers and alone reads them there.
+constexpr int CTL = NCT - 32;
+static_assert(KP_MAX <= CTL, "the control thread computes no z entry");
 constexpr int SRING = 128;                    // posted scan results
 
 struct Shared {
@@ -166,6 +172,15 @@ __device__ __forceinline__ int ld_acquire(const int *p)
     return v;
 }
 
+// the same at CTA scope, for flags in shared memory: the "memory" clobber
+// also keeps the compiler from hoisting later loads above it
+__device__ __forceinline__ int ld_acquire_cta(const volatile int *p)
+{
+    int v;
+    asm volatile("ld.acquire.cta.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
 __device__ void raise_timeout(const PanelParams &P)
 {
     atomicExch(P.status, LDLT_ERR_TIMEOUT_CODE);
@@ -176,11 +191,12 @@ __device__ void raise_timeout(const PanelParams &P)
 __device__ __forceinline__ uint32_t zval(int k, const uint32_t *u, int stride, const Shared &sh, const FieldP &f)
 {
     const uint8_t kd = sh.kind[k];
-    if (kd == K_1x1) return fp_mul(u[k * stride], sh.bw[k], f);
-    if (kd == K_2A)
-        return fp_mul(fp_sub(fp_mul(sh.mx[k], u[(k + 1) * stride], f), fp_mul(sh.my[k], u[k * stride], f), f),
-                      sh.bw[k], f);
-    return fp_mul(fp_mul(sh.mx[k - 1], u[(k - 1) * stride], f), sh.bw[k - 1], f);
+    const int kb = k - (kd == K_2B);               // the block's first column
+    const int j = k + (kd == K_2A) - (kd == K_2B);
+    const uint32_t c1 = kd == K_1x1 ? 1u : sh.mx[kb];
+    const uint32_t c2 = kd == K_2A ? sh.my[k] : 0u;
+    const uint32_t t = fp_sub(fp_mul(c1, u[j * stride], f), fp_mul(c2, u[k * stride], f), f);
+    return fp_mul(t, sh.bw[kb], f);
 }
 
 // c~_z[t] = W S(t, a) - sum_{k < np} U~[t][k] z[k], two threads per row (half
@@ -600,7 +616,7 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
             }
         }
     };
-    // thread 0: take in answered scans, oldest first; posts the new head and
+    // thread CTL: take in answered scans, oldest first; posts the new head and
     // a rollback request (index of the scan that found a partner, or -1)
     auto check_scans = [&](bool wait_oldest) {
         if (wait_oldest && ph < pt) {
@@ -616,7 +632,8 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
         int q = ph, rb = -1, rb_b = 0;
         while (q < pt) {
             const int id = sh.pend_id[q % NPEND];
-            if (sh.scan_resolved <= id) break;
+            // the answer is read only after the flag that publishes it
+            if (ld_acquire_cta(&sh.scan_resolved) <= id) break;
             const int v = sh.res_min[id % SRING];
             if (v >= w && v < P.m) { rb = q; rb_b = v; break; }
             ++q;  // confirmed: that row is a zero row
@@ -666,7 +683,7 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
         const bool full = np > P.kp - 2 || ia >= w || ev_next > MAX_EVENTS - 64 || nscan > MAX_SCANS - 64;
         if (full) {
             if (ph == pt) break;  // nothing in flight: the panel is complete
-            if (tid == 0) check_scans(true);
+            if (tid == CTL) check_scans(true);
             cbar();
             ph = sh.ph_new;
             const int rb = sh.rb, rb_b = sh.rb_b;
@@ -688,12 +705,8 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
         if (tid < np) {
             ring_ready(ev_next);
             za[tid] = zval(tid, sh.U + a, SSTRIDE, sh, f);
-            // Snapshot for a rollback to this row, kept only if its scan is issued.
-            // With NPEND scans pending, slot pt % NPEND is still the oldest
-            // scan's snapshot: leave it (this row then waits and is retried).
-            if (pt - ph < NPEND) sh.pend_bw[pt % NPEND][tid] = sh.bw[tid];
         }
-        if (tid == 0) {
+        if (tid == CTL) {
             sh.dbg[0] += 1;
             check_scans(false);
         }
@@ -722,6 +735,12 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
                 continue;
             }
         }
+        // Snapshot for a rollback to this row, kept if its scan is issued.  It
+        // is taken after the head update above, with the head the scan path
+        // tests: a scan goes out only while pt - ph < npend <= NPEND, so slot
+        // pt % NPEND then holds no pending scan's snapshot and always holds
+        // this row's.
+        if (tid < np && pt - ph < NPEND) sh.pend_bw[pt % NPEND][tid] = sh.bw[tid];
         lap(0);
         // c~_a[t] for the window rows t >= a (t = a included) and the first
         // non-zero of row a beyond a inside the window, in one pass
@@ -789,7 +808,7 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
         if (b == INT_MAX && helpers) {
             // ---- speculative far scan: publish it and go on as if the row were zero ----
             if (pt - ph >= P.npend) {
-                if (tid == 0) check_scans(true);
+                if (tid == CTL) check_scans(true);
                 cbar();
                 ph = sh.ph_new;
                 const int rb = sh.rb, rb_b = sh.rb_b;
@@ -800,7 +819,7 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
                 lap(6);
                 continue;  // the row is taken again from the top
             }
-            if (tid == 0) {
+            if (tid == CTL) {
                 Event &ev = sh.ev[slot];
                 ev.kind = EV_SCAN; ev.a = a; ev.b = -1; ev.np = np; ev.s0 = W; ev.s1 = 0;
                 ev.scan_id = nscan; ev.pad = 0;
