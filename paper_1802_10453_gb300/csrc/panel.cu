@@ -357,8 +357,19 @@ __device__ void helper_cta(const PanelParams &P, Shared &sh, int lo, int hi)
                 // t > a for every far row t: column a of row t
                 const int c = ea & 3;
                 for (int lr = lane; lr < nr; lr += 32) sh.scol[s][0][lr] = pick4(sh.sgrp[bi][lr], c);
-                if (kind == EV_PIVOT2)
-                    for (int lr = lane; lr < nr; lr += 32) sh.scol[s][1][lr] = s_at(P.S, P.ldS, lo + lr, eb);
+                if (kind == EV_PIVOT2) {
+                    // S(t, b): for t > b one line per row, so all loads of the
+                    // lane go out before the first store (one round trip)
+                    uint32_t v[SROWS / 32];
+#pragma unroll
+                    for (int i = 0; i < SROWS / 32; ++i) {
+                        const int lr = lane + 32 * i;
+                        v[i] = lr < nr ? s_at(P.S, P.ldS, lo + lr, eb) : 0u;
+                    }
+#pragma unroll
+                    for (int i = 0; i < SROWS / 32; ++i)
+                        if (lane + 32 * i < nr) sh.scol[s][1][lane + 32 * i] = v[i];
+                }
                 __syncwarp();
                 if (gbuf_g[bi ^ 1] != g + 1) {
                     // prefetch the next group into the other buffer once nothing is in flight
@@ -851,6 +862,12 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
         }
 
         // ---- 2x2 pivot on (a, b) ----
+        // S(a, b) and S(b, b) for x~ and y~, loaded before the z work below
+        uint32_t s_ab = 0u, s_bb = 0u;
+        if (tid == 0) {
+            s_ab = s_at(P.S, P.ldS, a, b);
+            s_bb = s_at(P.S, P.ldS, b, b);
+        }
         if (!far && tid < np) sh.ub[tid] = sh.U[tid * SSTRIDE + b];
         cbar();
         if (tid < np) zb[tid] = zval(tid, sh.ub, 1, sh, f);
@@ -868,8 +885,8 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
                 sy += __shfl_xor_sync(0xffffffffu, sy, o);
             }
             if (lane == 0) {
-                sh.xy[0] = fp_sub(fp_mul(W, s_at(P.S, P.ldS, a, b), f), fp_reduce64(sx, f), f);
-                sh.xy[1] = fp_sub(fp_mul(W, s_at(P.S, P.ldS, b, b), f), fp_reduce64(sy, f), f);
+                sh.xy[0] = fp_sub(fp_mul(W, s_ab, f), fp_reduce64(sx, f), f);
+                sh.xy[1] = fp_sub(fp_mul(W, s_bb, f), fp_reduce64(sy, f), f);
             }
         }
         // c~_b[t] for the window rows t >= a (overlaps warp 0's work)

@@ -279,6 +279,19 @@ def test_planted_n28000_full_scan_fifo():
     _check_planted_full_size(28000, 14000, False, 65521, 91 + 28000, lr.PATH_TC)
 
 
+@pytest.mark.parametrize("depth", [1, 2, 5, 16])
+def test_planted_speculation_depths(depth):
+    """Every speculation depth gives the same exact result.  Small depths keep
+    the FIFO of speculative scans full, so rows wait for the oldest scan, are
+    retaken and roll back to snapshots taken in rows where the FIFO head
+    moved."""
+    lr.set_speculation(depth)
+    try:
+        _check_planted_full_size(12000, 6000, False, 65521, 17 + depth, lr.PATH_TC)
+    finally:
+        lr.set_speculation(16)
+
+
 def test_wait_budget_timeout_reports_status():
     """A wait that runs out is reported in the device status word, and the
     context stays usable for the next call."""
