@@ -48,9 +48,12 @@ struct PanelSync {
 // Answer to one far scan: helpers lower `min` to their first non-zero row and
 // then count themselves in `done` (initialised to done = 0, min = INT_MAX).
 struct ScanSlot {
-    int done;
-    int min;
+    int done;           // helpers that answered
+    int min;            // smallest row with a non-zero entry, INT_MAX if none yet
+    unsigned mask[8];   // bit h: helper CTA h answered (its min is in above)
+    int pad[6];
 };
+static_assert(MAX_PANEL_GRID <= 8 * 32, "one answer bit per helper CTA");
 
 // What the panel kernel reports back to the host.
 struct PanelOut {

@@ -111,10 +111,10 @@ __device__ __forceinline__ void mac(uint64_t &acc, uint32_t a, uint32_t b, const
 }
 
 constexpr int NPEND = 16;                     // speculative far scans in flight
-// The far-scan bookkeeping (issue, answers, rollback requests) runs on one
-// thread of the last compute warp, which holds no z entry (np <= KP_MAX < CTL),
-// so it overlaps the z vector of the first warps.  It alone writes the pend_*
-// records between barriers and alone reads them there.
+// The far-scan bookkeeping (issue, answers, rollback requests) runs on the
+// last compute warp, which holds no z entry (np <= KP_MAX <= CTL), so it
+// overlaps the z vector of the first warps.  Its lane 0 (CTL) alone writes the
+// pend_* records; between barriers only that warp reads them.
 constexpr int CTL = NCT - 32;
 static_assert(KP_MAX <= CTL, "the control thread computes no z entry");
 constexpr int SRING = 128;                    // posted scan results
@@ -147,6 +147,7 @@ struct Shared {
     uint32_t pend_bw[NPEND][KP_MAX];   // w_B when the scan was issued
     uint32_t delta[KP_MAX];            // delta_B at the block's first column
     int res_min[SRING];
+    volatile int res_ok[SRING];        // id + 1 once scan id's answer is in res_min
     int redi[32];
     uint32_t xy[4];
     uint32_t caa;
@@ -155,7 +156,6 @@ struct Shared {
     volatile int quit;
     volatile int ev_fetched;           // helpers: event records fetched (poller -> column loader)
     volatile int nscan_pub;            // scans published (leader -> watcher warp)
-    volatile int scan_resolved;        // scans answered by every helper (watcher -> leader)
     uint32_t W;
     int np, ia, nzero, nscan, abort, b, owner, nblk;
     int ph_new, rb, rb_b;              // posted by thread 0: pending head, rollback request
@@ -172,7 +172,16 @@ __device__ __forceinline__ int ld_acquire(const int *p)
     return v;
 }
 
-// the same at CTA scope, for flags in shared memory: the "memory" clobber
+// relaxed load at GPU scope: a flag read that a later fence can turn into an
+// acquire
+__device__ __forceinline__ unsigned ld_relaxed(const void *p)
+{
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// acquire load at CTA scope, for flags in shared memory: the "memory" clobber
 // also keeps the compiler from hoisting later loads above it
 __device__ __forceinline__ int ld_acquire_cta(const volatile int *p)
 {
@@ -478,10 +487,13 @@ __device__ void helper_cta(const PanelParams &P, Shared &sh, int lo, int hi)
                 if (tid == 0) {
                     atomicMin(&P.scans[sid].min, mn);
                     __threadfence();
+                    atomicOr(&P.scans[sid].mask[blockIdx.x >> 5], 1u << (blockIdx.x & 31));
                     atomicAdd(&P.scans[sid].done, 1);
                 }
             } else if (tid == 0) {
-                atomicAdd(&P.scans[sid].done, 1);  // a miss: nothing to order before the count
+                // a miss: nothing to order before the answer bit and the count
+                atomicOr(&P.scans[sid].mask[blockIdx.x >> 5], 1u << (blockIdx.x & 31));
+                atomicAdd(&P.scans[sid].done, 1);
             }
         }
         cbar();
@@ -501,10 +513,11 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
     const int w = P.w;
     const int nh = gridDim.x - 1;
     for (int t = tid; t < W0; t += blockDim.x) sh.wstate[t] = 0;
+    for (int i = tid; i < SRING; i += blockDim.x) sh.res_ok[i] = 0;
     if (tid == 0) {
         sh.np = 0; sh.ia = 0; sh.nzero = 0; sh.nscan = 0; sh.abort = 0; sh.nblk = 0;
         sh.ev_ready = 0; sh.ev_done = 0; sh.quit = 0; sh.W = 1u;
-        sh.nscan_pub = 0; sh.scan_resolved = 0; sh.ph_new = 0;
+        sh.nscan_pub = 0; sh.ph_new = 0;
         sh.rb = -1; sh.nrollback = 0;
         for (int i = 0; i < 16; ++i) sh.dbg[i] = 0;
     }
@@ -541,10 +554,14 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
                     if (kind == EV_END || kk < np) rec[8 + k] = sh.ring[s][k];
                 }
                 if (lane < 8) rec[lane] = reinterpret_cast<const uint32_t *>(&sh.ev[s])[lane];
-                if (kind == EV_SCAN && lane == 0) {
-                    P.scans[sh.ev[s].scan_id].done = 0;
-                    P.scans[sh.ev[s].scan_id].min = INT_MAX;
-                    last_scan = sh.ev[s].scan_id;
+                if (kind == EV_SCAN) {
+                    const int sid = sh.ev[s].scan_id;
+                    if (lane < 8) P.scans[sid].mask[lane] = 0u;
+                    if (lane == 0) {
+                        P.scans[sid].done = 0;
+                        P.scans[sid].min = INT_MAX;
+                    }
+                    last_scan = sid;
                 }
                 end = end || (kind == EV_END);
             }
@@ -563,37 +580,80 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
         }
     }
     if (warp == NCW) {
-        // ---- watcher: posts the answers of the far scans, in order ----
+        // ---- watcher: posts the answers of the far scans ----
+        // Lane i probes scan base + i, so up to 32 published scans are watched
+        // at once and each answer is posted as soon as it is final: a miss
+        // once every helper answered; a hit at row v once the helpers owning
+        // the rows below v answered (no smaller row can still come), which
+        // is usually well before the last helper is done.
         if (!helpers) return;
-        for (int id = 0;; ++id) {
-            int go = 0, v = INT_MAX;
-            if (lane == 0) {
-                Spin sp;
-                for (;;) {
-                    if (sh.nscan_pub > id) { go = 1; break; }
-                    if (sh.quit) break;
-                    __nanosleep(32);
-                    if (sp.expired(4 * P.budget_ns + 1000000)) break;
+        const int chunk = (P.m - w + nh - 1) / nh;  // far rows per helper, as in helper_cta
+        volatile int *ab = &P.sync->abort;
+        int base = 0;
+        unsigned posted = 0u;  // bit i: scan base + i posted
+        Spin sp;
+        for (;;) {
+            const int npub = sh.nscan_pub;
+            const int id = base + lane;
+            bool ok = false;
+            if (id < npub && !((posted >> lane) & 1u)) {
+                const ScanSlot *sl = P.scans + id;
+                int v = INT_MAX;
+                if (ld_acquire(&sl->done) >= nh) {
+                    v = __ldcg(&sl->min);
+                    ok = true;
+                } else {
+                    const int m = (int)ld_relaxed(&sl->min);
+                    if (m != INT_MAX) {
+                        const int owner = 1 + (m - w) / chunk;
+                        bool all = true;
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            if (32 * i > owner) break;
+                            const int b0 = 32 * i < 1 ? 1 : 32 * i;
+                            const int b1 = 32 * i + 31 < owner ? 32 * i + 31 : owner;
+                            const unsigned need = (b1 - 32 * i == 31 ? 0xffffffffu : ((2u << (b1 - 32 * i)) - 1u)) &
+                                                  ~((1u << (b0 - 32 * i)) - 1u);
+                            const unsigned got = ld_relaxed(&sl->mask[i]);
+                            all = all && ((got & need) == need);
+                        }
+                        if (all) {
+                            // every helper below owner answered; acquire their
+                            // mins, then the smallest row is final
+                            asm volatile("fence.acq_rel.gpu;" ::: "memory");
+                            v = (int)ld_relaxed(&sl->min);
+                            ok = true;
+                        }
+                    }
                 }
-                if (go) {
-                    go = 0;
-                    volatile int *ab = &P.sync->abort;
-                    Spin sp2;
-                    for (;;) {
-                        if (ld_acquire(&P.scans[id].done) >= nh) { go = 1; break; }
-                        if (*ab || sh.quit) break;
-                        if (sp2.expired(P.budget_ns)) { raise_timeout(P); break; }
-                    }
-                    if (go) {
-                        v = __ldcg(&P.scans[id].min);  // ordered after the acquire above
-                        sh.res_min[id % SRING] = v;
-                        __threadfence_block();
-                        sh.scan_resolved = id + 1;
-                    }
+                if (ok) {
+                    sh.res_min[id % SRING] = v;
+                    __threadfence_block();
+                    sh.res_ok[id % SRING] = id + 1;
                 }
             }
-            go = __shfl_sync(0xffffffffu, go, 0);
-            if (!go) return;
+            const unsigned okm = __ballot_sync(0xffffffffu, ok);
+            posted |= okm;
+            const int adv = (posted == 0xffffffffu) ? 32 : __ffs(~posted) - 1;
+            base += adv;
+            posted = (adv == 32) ? 0u : (posted >> adv);
+            if (okm) {
+                sp = Spin();
+                continue;
+            }
+            if (sh.quit) return;
+            // lane 0 decides for the warp when to give up
+            int stop = 0;
+            if (lane == 0) {
+                if (base < npub) {
+                    if (*ab) stop = 1;
+                    else if (sp.expired(P.budget_ns)) { raise_timeout(P); stop = 1; }
+                } else {
+                    __nanosleep(32);
+                    if (sp.expired(4 * P.budget_ns + 1000000)) stop = 1;
+                }
+            }
+            if (__shfl_sync(0xffffffffu, stop, 0)) return;
         }
     }
 
@@ -627,31 +687,46 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
             }
         }
     };
-    // thread CTL: take in answered scans, oldest first; posts the new head and
-    // a rollback request (index of the scan that found a partner, or -1)
+    // the control warp (lane 0 is CTL): take in the answered scans.  Posts
+    // the new head (the first pending scan that is unanswered or found a
+    // partner) and a rollback request: the earliest answered scan that found a
+    // partner (-1 if none), even while older scans are still unanswered; they
+    // stay pending and may roll the panel back further.
+    auto resolved = [&](int id) { return ld_acquire_cta(&sh.res_ok[id % SRING]) == id + 1; };
     auto check_scans = [&](bool wait_oldest) {
+        __syncwarp();  // the pend_* records written by CTL
         if (wait_oldest && ph < pt) {
-            const int id = sh.pend_id[ph % NPEND];
-            Spin sp;
-            while (sh.scan_resolved <= id) {
-                __nanosleep(16);
-                if (sp.expired(P.budget_ns)) { raise_timeout(P); sh.abort = 1; break; }
+            if (lane == 0) {
+                const int id = sh.pend_id[ph % NPEND];
+                Spin sp;
+                while (!resolved(id)) {
+                    __nanosleep(16);
+                    if (sp.expired(P.budget_ns)) { raise_timeout(P); sh.abort = 1; break; }
+                }
+                sh.dbg[1] += 1;
             }
-            sh.dbg[1] += 1;
+            __syncwarp();
         }
-        __threadfence_block();
-        int q = ph, rb = -1, rb_b = 0;
-        while (q < pt) {
+        const int q = ph + lane;  // pt - ph <= NPEND < 32
+        bool res = false, hit = false;
+        int v = 0;
+        if (q < pt) {
             const int id = sh.pend_id[q % NPEND];
-            // the answer is read only after the flag that publishes it
-            if (ld_acquire_cta(&sh.scan_resolved) <= id) break;
-            const int v = sh.res_min[id % SRING];
-            if (v >= w && v < P.m) { rb = q; rb_b = v; break; }
-            ++q;  // confirmed: that row is a zero row
+            if (resolved(id)) {  // the answer is read only after its flag
+                res = true;
+                v = sh.res_min[id % SRING];
+                hit = v >= w && v < P.m;
+            }
         }
-        sh.ph_new = q;
-        sh.rb = rb;
-        sh.rb_b = rb_b;
+        const unsigned rm = __ballot_sync(0xffffffffu, res), hm = __ballot_sync(0xffffffffu, hit);
+        const int head = __ffs(~rm | hm) - 1;
+        const int first = hm ? __ffs(hm) - 1 : -1;
+        const int vb = __shfl_sync(0xffffffffu, v, first < 0 ? 0 : first);
+        if (lane == 0) {
+            sh.ph_new = ph + head;
+            sh.rb = first < 0 ? -1 : ph + first;
+            sh.rb_b = vb;
+        }
     };
     // all compute threads: roll back to pending scan k, which found partner b
     auto rollback = [&](int k, int bfound) {
@@ -679,7 +754,7 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
         W = sh.pend_W[slot];
         force_b = bfound;
         force_sid = sh.pend_id[slot];
-        pt = k;  // this and every later pending scan are dropped (ph == k)
+        pt = k;  // this and every later pending scan are dropped; older ones stay
         ++nrb;
         cbar();
     };
@@ -694,7 +769,7 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
         const bool full = np > P.kp - 2 || ia >= w || ev_next > MAX_EVENTS - 64 || nscan > MAX_SCANS - 64;
         if (full) {
             if (ph == pt) break;  // nothing in flight: the panel is complete
-            if (tid == CTL) check_scans(true);
+            if (warp == NCW - 1) check_scans(true);
             cbar();
             ph = sh.ph_new;
             const int rb = sh.rb, rb_b = sh.rb_b;
@@ -717,8 +792,8 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
             ring_ready(ev_next);
             za[tid] = zval(tid, sh.U + a, SSTRIDE, sh, f);
         }
-        if (tid == CTL) {
-            sh.dbg[0] += 1;
+        if (warp == NCW - 1) {
+            if (lane == 0) sh.dbg[0] += 1;
             check_scans(false);
         }
         const bool myrow = inwin && lr >= a;
@@ -819,7 +894,7 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
         if (b == INT_MAX && helpers) {
             // ---- speculative far scan: publish it and go on as if the row were zero ----
             if (pt - ph >= P.npend) {
-                if (tid == CTL) check_scans(true);
+                if (warp == NCW - 1) check_scans(true);
                 cbar();
                 ph = sh.ph_new;
                 const int rb = sh.rb, rb_b = sh.rb_b;
