@@ -42,4 +42,4 @@ from .binding import (  # noqa: F401
     set_speculation,
     effective_ops,
 )
-from .tune import tune_batched  # noqa: E402,F401
+from .tune import OnlineTuner, tune_batched  # noqa: E402,F401

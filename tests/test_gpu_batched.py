@@ -229,3 +229,28 @@ def test_autotuner_keeps_results_and_inputs():
         lr.set_batched_schedule(32, 0, 32)
     for i, A in enumerate(mats):
         _assert_oracle(A, p, _out(batch, i))
+
+
+def test_online_tuner_over_a_stream_matches_the_oracle():
+    """A stream of batches through OnlineTuner: every candidate is tried on a
+    real batch, times are taken in, and every matrix of every batch is exactly
+    the oracle's, whichever schedule ran it."""
+    p = 65521
+    cands = ((32, 0, 32), (16, 0, 16), (32, 200, 16))
+    tuner = lr.OnlineTuner(p, candidates=cands, explore_every=3)
+    try:
+        for j in range(7):
+            ns, mats = _mixed_batch(p, 4242 + j, extra=4)
+            batch = lr.Batch(ns)
+            _fill_host(batch, mats)
+            tuner.factor(batch)
+            torch.cuda.synchronize()
+            for i in range(0, len(mats), 3):
+                _assert_oracle(mats[i], p, _out(batch, i))
+            assert int((batch.status != 0).sum().item()) == 0
+        tuner.flush()
+    finally:
+        lr.set_batched_schedule(32, 0, 32)
+    assert [c for _, c in tuner.history[:3]] == list(cands)
+    assert set(tuner.cost) == set(cands) and all(v > 0 for v in tuner.cost.values())
+    assert tuner.best in cands
