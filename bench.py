@@ -46,10 +46,8 @@ def parse():
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    from paper_1802_10453_gb300.replicas import dist_env as _env
+    return _env()
 
 
 def tc_digits(p):
@@ -397,15 +395,11 @@ def main():
     prof = (ctypes.c_double * 32)()
     L.ldlt_rpm_profile_read(prof)
     prof = list(prof)
-    ms_total = ev0.elapsed_time(ev1)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    from paper_1802_10453_gb300.replicas import max_over_ranks, whole_job_rate
+    ms_total = max_over_ranks(ev0.elapsed_time(ev1), world, device=dev)
     ms_step = ms_total / args.steps
     ops = effective_ops(n, rank_found)
-    value = ops * world / (ms_step * 1e-3) / 1e9
+    value = whole_job_rate(ops, world, ms_step * 1e-3) / 1e9
 
     # parity of the timed output: R_A must be the planted supp(R)
     rpm = lr.rpm_from_factor(res).cpu().numpy()
