@@ -509,6 +509,34 @@ def main():
         solve_line = {"n": n, "by_nrhs": sv, "form": "blocked forward/backward substitution, 64-row blocks",
                       "note": "random B (consistency not required for timing)"}
 
+    # Algorithm 1 (TRSS): X^T U + U^T X = C at n = 4096 over the paper's 23-bit prime
+    trss_line = None
+    if rank == 0:
+        nt, pt = 4096, 8388593
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(1802)
+        Ut = torch.randint(0, pt, (nt, nt), dtype=torch.int32, device=dev, generator=gen).triu_()
+        Ut.diagonal().copy_(torch.randint(1, pt, (nt,), dtype=torch.int32, device=dev, generator=gen))
+        C0 = torch.randint(0, pt, (nt, nt), dtype=torch.int32, device=dev, generator=gen)
+        Ct = torch.empty_like(C0)
+        ms_t = []
+        for it in range(4):
+            Ct.copy_(C0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st_t = lr.trss(Ut, Ct, pt, stream=stream, check=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if it:
+                ms_t.append(e0.elapsed_time(e1))
+        ms_tr = statistics.median(ms_t)
+        macs = nt ** 3 / 3.0  # the SYR2K updates dominate: sum over blocks of b (n - k)^2
+        trss_line = {"n": nt, "p": pt, "ms": ms_tr, "gmac_per_s": macs / (ms_tr * 1e-3) / 1e9,
+                     "status": int(st_t.item()),
+                     "form": "blocked right-looking (32-row blocks): diagonal TRSS, panel TRMM+TRSM, "
+                             "SYR2K on CUDA cores, 64-bit exact accumulation"}
+
     batched = None
     if rank == 0 and not args.no_batched:
         batched = batched_bench(lr, inputs, inputs_gpu, dev, max(3, min(args.steps, 10)))
@@ -537,6 +565,7 @@ def main():
             "fp64_form": fp64,
             "batched": batched,
             "solve": solve_line,
+            "trss": trss_line,
             "cpu_baseline": cpu}
     if rank == 0:
         print(json.dumps(line), flush=True)

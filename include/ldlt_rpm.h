@@ -140,6 +140,31 @@ int ldlt_rpm_solve(int64_t n, uint32_t p, const uint32_t *A, int64_t lda,
                    void *ws, size_t ws_bytes, void *stream);
 
 /*
+ * ldlt_rpm_trss -- Algorithm 1 (TRSS) of Section 4, Problem 1: the upper
+ * triangular X with X^T U + U^T X = C over Z/pZ, the routine Algorithm 3
+ * uses to eliminate the leading block of Q C Q^T with the pivots of B.
+ *
+ *   n        order (>= 0).
+ *   p        prime, 2 <= p < 2^31.  For p = 2 a solution exists only when the
+ *            diagonal met at each step is zero (the diagonal of X^T U + U^T X
+ *            is zero in characteristic 2); x_ii = 0 is taken there.
+ *   U, ldu   n x n upper triangular with a non-zero diagonal, row-major; only
+ *            the upper triangle (i <= j) is read; entries reduced mod p.
+ *   C, ldc   n x n symmetric, row-major; its upper triangle (i <= j) is read
+ *            and overwritten by X (in place); the strict lower triangle is
+ *            not touched.
+ *   status   int32[1]: 0; LDLT_ERR_ARG if U has a zero diagonal entry;
+ *            LDLT_ERR_INCONSISTENT if p = 2 and no solution exists.  X is
+ *            undefined then.
+ *   stream   cudaStream_t as void*; three launches per 32-row block are
+ *            enqueued, nothing is read back.
+ * Returns LDLT_OK, LDLT_ERR_ARG (n < 0, ld < n, NULL pointer),
+ * LDLT_ERR_NOT_PRIME, LDLT_ERR_P_RANGE or LDLT_ERR_CUDA.
+ */
+int ldlt_rpm_trss(int64_t n, uint32_t p, const uint32_t *U, int64_t ldu,
+                  uint32_t *C, int64_t ldc, int32_t *status, void *stream);
+
+/*
  * ldlt_rpm_strict -- the strict form of a characteristic-2 factorisation
  * (Section 2.2, "Antitriangular decomposition"), in place on the outputs of
  * ldlt_rpm_factor / ldlt_rpm_factor_batched for the same A.

@@ -37,6 +37,7 @@ from .binding import (  # noqa: F401
     rpm_from_factor,
     strict,
     solve,
+    trss,
     LDLT_ERR_INCONSISTENT,
     set_wait_budget_ns,
     set_speculation,

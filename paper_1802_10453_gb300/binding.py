@@ -35,7 +35,7 @@ NOALLOC_BYTES = 48 << 20
 EXPORTS = ["ldlt_rpm_workspace_bytes", "ldlt_rpm_factor", "rpm_from_factor", "ldlt_rpm_version",
            "ldlt_rpm_set_wait_budget_ns", "ldlt_rpm_set_speculation", "ldlt_rpm_factor_noalloc",
            "ldlt_rpm_factor_batched", "ldlt_rpm_batched_workspace_bytes", "ldlt_rpm_batched_set_schedule",
-           "ldlt_rpm_strict", "ldlt_rpm_solve"]
+           "ldlt_rpm_strict", "ldlt_rpm_solve", "ldlt_rpm_trss"]
 BATCH_MAX_N = 512  # LDLT_BATCH_MAX_N
 
 
@@ -83,6 +83,8 @@ def lib():
                                          c_i64, c_vp, c_vp, c_sz, c_vp]
             L.ldlt_rpm_strict.restype = ctypes.c_int
             L.ldlt_rpm_strict.argtypes = [c_i64, c_u32, c_vp, c_i64, c_vp, c_vp, c_vp]
+            L.ldlt_rpm_trss.restype = ctypes.c_int
+            L.ldlt_rpm_trss.argtypes = [c_i64, c_u32, c_vp, c_i64, c_vp, c_i64, c_vp, c_vp]
             L.rpm_from_factor.restype = ctypes.c_int
             L.rpm_from_factor.argtypes = [c_i64, c_vp, c_vp, c_vp, c_vp, c_vp]
             L.ldlt_rpm_version.restype = ctypes.c_int
@@ -350,6 +352,33 @@ def strict(A, res: dict, stream=None) -> dict:
     if rc != LDLT_OK:
         raise LdltError(rc, "ldlt_rpm_strict")
     return res
+
+
+def trss(U, C, p: int, stream=None, check: bool = True):
+    """ldlt_rpm_trss (Algorithm 1): X upper triangular with X^T U + U^T X = C.
+    U and C are square CUDA int32/uint32 tensors of the same order (U's upper
+    triangle and C's upper triangle are read); C's upper triangle is
+    overwritten by X in place.  Returns the device status tensor; with
+    check=True waits for the stream and raises if it is non-zero."""
+    import torch
+    n = int(U.shape[0])
+    if tuple(U.shape) != (n, n) or tuple(C.shape) != (n, n):
+        raise LdltError(LDLT_ERR_ARG, "U and C must be square of one order")
+    dev = C.device
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    ldu = U.stride(0) if n > 0 else 1
+    ldc = C.stride(0) if n > 0 else 1
+    rc = lib().ldlt_rpm_trss(n, int(p), U.data_ptr(), ldu, C.data_ptr(), ldc, st.data_ptr(), stream.cuda_stream)
+    if rc != LDLT_OK:
+        raise LdltError(rc, "ldlt_rpm_trss")
+    if check:
+        stream.synchronize()
+        code = int(st.item())
+        if code != 0:
+            raise LdltError(code, "ldlt_rpm_trss device status")
+    return st
 
 
 def rpm_from_factor(res: dict, stream=None):

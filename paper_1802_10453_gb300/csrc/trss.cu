@@ -1,0 +1,208 @@
+// trss.cu -- Algorithm 1 (TRSS, Problem 1): the upper triangular X with
+// X^T U + U^T X = C over Z/pZ, for U upper triangular with a non-zero
+// diagonal and C symmetric.  X overwrites C's upper triangle in place (the
+// remark after Algorithm 1).
+//
+// Algorithm 1 halves recursively: X1 from (U1, C1); D2 = C2 - X1^T U2 (TRMM);
+// X2 = U1^{-T} D2 (TRSM); D3 = C3 - (X2^T U2 + U2^T X2) (SYR2K); X3 from
+// (U3, D3).  Unrolled over blocks of TB rows from the top it is the
+// right-looking form run here, three launches per block k (rows [k0, k1)):
+//   trss_diag_kernel   X_kk from U_kk and C_kk: the same steps with blocks of
+//                      one row, in one CTA (x_ii = c_ii / (2 u_ii), the row
+//                      to its right, a rank-2 update of the rest of the block)
+//   trss_panel_kernel  X_k,r = U_kk^{-T} (C_k,r - X_kk^T U_k,r) for the
+//                      columns r >= k1, 64 columns per CTA
+//   trss_syr2k_kernel  C_r,r -= X_k,r^T U_k,r + U_k,r^T X_k,r on the upper
+//                      triangle of the trailing block, 64 x 64 tiles
+// Characteristic 2: the diagonal of X^T U + U^T X is zero, so a solution
+// exists only if C's diagonal (after the updates) is zero; x_ii = 0 is taken
+// and a non-zero diagonal entry is reported as LDLT_ERR_INCONSISTENT.
+// Arithmetic: residues < p < 2^31, exact 64-bit products; sums are folded
+// below 2^63 by subtracting a multiple of p (field.cuh), reduced once.
+#include <cstdint>
+
+#include "../../include/ldlt_rpm.h"
+#include "ldlt_internal.cuh"
+
+namespace {
+
+constexpr int TB = 32;      // rows per block step
+constexpr int TC = 64;      // columns per CTA in the panel and trailing kernels
+
+__device__ __forceinline__ uint32_t rd(const uint32_t *M, int64_t ld, int64_t i, int64_t j, const FieldP &f)
+{
+    const uint32_t v = M[i * ld + j];
+    return v >= f.p ? v % f.p : v;
+}
+
+// X_kk: TB x TB (nb x nb used) in one CTA of TB * TB threads.
+__global__ void __launch_bounds__(TB * TB) trss_diag_kernel(int64_t k0, int nb, const uint32_t *U, int64_t ldu,
+                                                            uint32_t *C, int64_t ldc, int32_t *status, FieldP f)
+{
+    __shared__ uint32_t u[TB][TB + 1], c[TB][TB + 1], uinv[TB];
+    const int tx = threadIdx.x % TB, ty = threadIdx.x / TB;  // (row ty, column tx)
+    const bool in = ty < nb && tx < nb && ty <= tx;
+    u[ty][tx] = in ? rd(U, ldu, k0 + ty, k0 + tx, f) : 0u;
+    c[ty][tx] = in ? rd(C, ldc, k0 + ty, k0 + tx, f) : 0u;
+    __syncthreads();
+    if (threadIdx.x < nb) {
+        const uint32_t d = u[threadIdx.x][threadIdx.x];
+        if (d == 0u) {
+            atomicExch(status, LDLT_ERR_ARG);
+            uinv[threadIdx.x] = 0u;
+        } else {
+            uinv[threadIdx.x] = fp_inv(d, f);
+        }
+    }
+    __syncthreads();
+    for (int i = 0; i < nb; ++i) {
+        // x_ii, then the rest of row i: x_ij = (c_ij - x_ii u_ij) / u_ii
+        __shared__ uint32_t xii;
+        if (threadIdx.x == 0) {
+            const uint32_t cii = c[i][i];
+            if (f.p == 2u) {
+                if (cii != 0u) atomicExch(status, LDLT_ERR_INCONSISTENT);
+                xii = 0u;
+            } else {
+                xii = fp_mul(fp_mul(cii, f.inv2, f), uinv[i], f);
+            }
+            c[i][i] = xii;
+        }
+        __syncthreads();
+        if (ty == 0 && tx > i && tx < nb)
+            c[i][tx] = fp_mul(fp_sub(c[i][tx], fp_mul(xii, u[i][tx], f), f), uinv[i], f);
+        __syncthreads();
+        // rank-2 update of rows and columns > i: c_jl -= x_ij u_il + u_ij x_il
+        if (ty > i && ty <= tx && tx < nb) {
+            const uint64_t s = (uint64_t)c[i][ty] * u[i][tx] + (uint64_t)u[i][ty] * c[i][tx];
+            c[ty][tx] = fp_sub(c[ty][tx], fp_reduce64(s, f), f);
+        }
+        __syncthreads();
+    }
+    if (in) C[(k0 + ty) * ldc + k0 + tx] = c[ty][tx];
+}
+
+// X_k,r for the columns [c0, c0 + TC) of the trailing part: per column j,
+// t = C_k,j - X_kk^T U_k,j, then U_kk^T y = t by forward substitution.
+__global__ void __launch_bounds__(TC) trss_panel_kernel(int64_t k0, int nb, int64_t n, const uint32_t *U,
+                                                         int64_t ldu, uint32_t *C, int64_t ldc, FieldP f)
+{
+    __shared__ uint32_t u[TB][TB + 1], x[TB][TB + 1], uinv[TB];
+    const int64_t k1 = k0 + nb;
+    for (int q = threadIdx.x; q < TB * TB; q += blockDim.x) {
+        const int r = q / TB, s = q % TB;
+        const bool in = r < nb && s < nb && r <= s;
+        u[r][s] = in ? rd(U, ldu, k0 + r, k0 + s, f) : 0u;
+        x[r][s] = in ? C[(k0 + r) * ldc + k0 + s] : 0u;  // X_kk, already reduced
+    }
+    __syncthreads();
+    if (threadIdx.x < nb) {
+        const uint32_t d = u[threadIdx.x][threadIdx.x];
+        uinv[threadIdx.x] = d ? fp_inv(d, f) : 0u;
+    }
+    __syncthreads();
+    const int64_t j = k1 + (int64_t)blockIdx.x * TC + threadIdx.x;
+    if (j >= n) return;
+    uint32_t uc[TB], y[TB];
+#pragma unroll
+    for (int r = 0; r < TB; ++r) uc[r] = r < nb ? rd(U, ldu, k0 + r, j, f) : 0u;
+#pragma unroll
+    for (int i = 0; i < TB; ++i) {
+        if (i >= nb) break;
+        // t_i = c_ij - sum_{k <= i} x_ki u_kj ;  y_i = (t_i - sum_{k < i} u_ki y_k) / u_ii
+        uint64_t acc = 0;
+#pragma unroll
+        for (int k = 0; k < TB; ++k) {
+            if (k > i) break;
+            fp_mac(acc, x[k][i], uc[k], f);
+            if (k < i) fp_mac(acc, u[k][i], y[k], f);
+        }
+        const uint32_t t = fp_sub(rd(C, ldc, k0 + i, j, f), fp_reduce64(acc, f), f);
+        y[i] = fp_mul(t, uinv[i], f);
+    }
+#pragma unroll
+    for (int i = 0; i < TB; ++i)
+        if (i < nb) C[(k0 + i) * ldc + j] = y[i];
+}
+
+// C[i][j] -= sum_k (X[k][i] U[k][j] + U[k][i] X[k][j]) for k in the block,
+// k1 <= i <= j < n; one 64 x 64 tile per CTA, 4 x 4 outputs per thread.
+__global__ void __launch_bounds__(256) trss_syr2k_kernel(int64_t k0, int nb, int64_t n, const uint32_t *U,
+                                                          int64_t ldu, uint32_t *C, int64_t ldc, FieldP f)
+{
+    const int64_t k1 = k0 + nb;
+    const int bi = blockIdx.y, bj = blockIdx.x;
+    if (bi > bj) return;  // tiles wholly below the diagonal
+    const int64_t i0 = k1 + (int64_t)bi * TC, j0 = k1 + (int64_t)bj * TC;
+    __shared__ uint32_t xi[TB][TC], ui[TB][TC], xj[TB][TC], uj[TB][TC];
+    for (int q = threadIdx.x; q < TB * TC; q += blockDim.x) {
+        const int k = q / TC, c = q % TC;
+        const bool ki = k < nb;
+        const int64_t ci = i0 + c, cj = j0 + c;
+        xi[k][c] = (ki && ci < n) ? C[(k0 + k) * ldc + ci] : 0u;
+        ui[k][c] = (ki && ci < n) ? rd(U, ldu, k0 + k, ci, f) : 0u;
+        xj[k][c] = (ki && cj < n) ? C[(k0 + k) * ldc + cj] : 0u;
+        uj[k][c] = (ki && cj < n) ? rd(U, ldu, k0 + k, cj, f) : 0u;
+    }
+    __syncthreads();
+    const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;  // rows ty + 16a, columns tx + 16b
+    uint64_t acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0;
+    for (int k = 0; k < nb; ++k) {
+        uint32_t xa[4], ua[4], xb[4], ub[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            xa[a] = xi[k][ty + 16 * a];
+            ua[a] = ui[k][ty + 16 * a];
+            xb[a] = xj[k][tx + 16 * a];
+            ub[a] = uj[k][tx + 16 * a];
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                fp_mac(acc[a][b], xa[a], ub[b], f);
+                fp_mac(acc[a][b], ua[a], xb[b], f);
+            }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int64_t i = i0 + ty + 16 * a, j = j0 + tx + 16 * b;
+            if (i < n && j < n && i <= j) {
+                uint32_t *cp = C + i * ldc + j;
+                const uint32_t old = *cp >= f.p ? *cp % f.p : *cp;
+                *cp = fp_sub(old, fp_reduce64(acc[a][b], f), f);
+            }
+        }
+}
+
+}  // namespace
+
+extern "C" int ldlt_rpm_trss(int64_t n, uint32_t p, const uint32_t *U, int64_t ldu, uint32_t *C, int64_t ldc,
+                             int32_t *status, void *stream)
+{
+    size_t tmp = 0;
+    const int rc = ldlt_rpm_workspace_bytes(1, p, LDLT_PATH_TC, &tmp);  // p prime, in range
+    if (rc != LDLT_OK) return rc;
+    if (n < 0 || !status) return LDLT_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(status, 0, sizeof(int32_t), st) != cudaSuccess) return LDLT_ERR_CUDA;
+    if (n == 0) return LDLT_OK;
+    if (!U || !C || ldu < n || ldc < n) return LDLT_ERR_ARG;
+    const FieldP f = make_field(p);
+    for (int64_t k0 = 0; k0 < n; k0 += TB) {
+        const int nb = (int)((n - k0) < TB ? (n - k0) : TB);
+        trss_diag_kernel<<<1, TB * TB, 0, st>>>(k0, nb, U, ldu, C, ldc, status, f);
+        const int64_t rest = n - (k0 + nb);
+        if (rest <= 0) continue;
+        const unsigned gp = (unsigned)((rest + TC - 1) / TC);
+        trss_panel_kernel<<<gp, TC, 0, st>>>(k0, nb, n, U, ldu, C, ldc, f);
+        trss_syr2k_kernel<<<dim3(gp, gp), 256, 0, st>>>(k0, nb, n, U, ldu, C, ldc, f);
+    }
+    return cudaGetLastError() == cudaSuccess ? LDLT_OK : LDLT_ERR_CUDA;
+}
