@@ -126,7 +126,10 @@ __global__ void __launch_bounds__(TC) trss_panel_kernel(int64_t k0, int nb, int6
 }
 
 // C[i][j] -= sum_k (X[k][i] U[k][j] + U[k][i] X[k][j]) for k in the block,
-// k1 <= i <= j < n; one 64 x 64 tile per CTA, 4 x 4 outputs per thread.
+// k1 <= i <= j < n; one 64 x 64 tile per CTA, 4 x 4 outputs per thread.  For
+// p < 2^28 the 2 TB products of a block (each < 2^56) sum below 2^63 without
+// folding; larger p fold after every product.
+template <bool BIG>
 __global__ void __launch_bounds__(256) trss_syr2k_kernel(int64_t k0, int nb, int64_t n, const uint32_t *U,
                                                           int64_t ldu, uint32_t *C, int64_t ldc, FieldP f)
 {
@@ -164,8 +167,12 @@ __global__ void __launch_bounds__(256) trss_syr2k_kernel(int64_t k0, int nb, int
         for (int a = 0; a < 4; ++a)
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
-                fp_mac(acc[a][b], xa[a], ub[b], f);
-                fp_mac(acc[a][b], ua[a], xb[b], f);
+                if (BIG) {
+                    fp_mac(acc[a][b], xa[a], ub[b], f);
+                    fp_mac(acc[a][b], ua[a], xb[b], f);
+                } else {
+                    acc[a][b] += (uint64_t)xa[a] * ub[b] + (uint64_t)ua[a] * xb[b];
+                }
             }
     }
 #pragma unroll
@@ -202,7 +209,10 @@ extern "C" int ldlt_rpm_trss(int64_t n, uint32_t p, const uint32_t *U, int64_t l
         if (rest <= 0) continue;
         const unsigned gp = (unsigned)((rest + TC - 1) / TC);
         trss_panel_kernel<<<gp, TC, 0, st>>>(k0, nb, n, U, ldu, C, ldc, f);
-        trss_syr2k_kernel<<<dim3(gp, gp), 256, 0, st>>>(k0, nb, n, U, ldu, C, ldc, f);
+        if (p >= (1u << 28))
+            trss_syr2k_kernel<true><<<dim3(gp, gp), 256, 0, st>>>(k0, nb, n, U, ldu, C, ldc, f);
+        else
+            trss_syr2k_kernel<false><<<dim3(gp, gp), 256, 0, st>>>(k0, nb, n, U, ldu, C, ldc, f);
     }
     return cudaGetLastError() == cudaSuccess ? LDLT_OK : LDLT_ERR_CUDA;
 }
