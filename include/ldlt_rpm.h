@@ -140,6 +140,40 @@ int ldlt_rpm_solve(int64_t n, uint32_t p, const uint32_t *A, int64_t lda,
                    void *ws, size_t ws_bytes, void *stream);
 
 /*
+ * ldlt_rpm_factor_given -- the given-P mode: the L and D of P^T A P = L D L^T
+ * for a pivot order and block structure supplied by the caller, e.g. those of
+ * Algorithm 2/3 (Section 4), whose order can differ from Algorithm 4's.  For
+ * odd p they are unique once P and the blocks are fixed (a 2x2 block
+ * [[0, x], [x, y]] of the Schur complement has in-block entry y/(2x) and
+ * D block [[0, x], [x, 0]]); for p = 2 the block keeps [[0, x], [x, y]] and
+ * in-block entry 0 (the conventions of ldlt_rpm_factor).
+ *
+ *   n, p, A, lda, path, ws, stream   as for ldlt_rpm_factor; A's lower
+ *            triangle is read in the original order and overwritten with L
+ *            and D in the supplied order (layout of ldlt_rpm_factor).
+ *   perm     int32[n], in: perm[k] = original index of position k (a
+ *            permutation of 0..n-1); out: unchanged.
+ *   e        uint32[n], in: e[k] != 0 marks a 2x2 block (k, k+1); out: x of
+ *            each block, 0 elsewhere.
+ *   rank     int64[1], in: the number of pivot positions (blocks count two);
+ *            out: the same when the structure fits.
+ *   status   int32[1]: 0; LDLT_ERR_ARG if perm is not a permutation;
+ *            LDLT_ERR_INCONSISTENT if the structure does not fit A (a zero
+ *            1x1 pivot, a 2x2 start with a non-zero diagonal or a zero x, or a
+ *            non-zero Schur complement after the rank); LDLT_ERR_TIMEOUT as
+ *            for ldlt_rpm_factor.  Outputs are undefined when non-zero.
+ *   ws_bytes at least ldlt_rpm_given_workspace_bytes(n, p, path).
+ * Runs ldlt_rpm_factor's path on P^T A P gathered in its ingest pass:
+ * Algorithm 4's search takes the identity order there exactly when the
+ * structure fits, and the result is checked against the supplied one.
+ * Returns as ldlt_rpm_factor.
+ */
+int ldlt_rpm_given_workspace_bytes(int64_t n, uint32_t p, int path, size_t *bytes);
+int ldlt_rpm_factor_given(int64_t n, uint32_t p, uint32_t *A, int64_t lda,
+                          int32_t *perm, uint32_t *e, int64_t *rank, int32_t *status,
+                          int path, void *ws, size_t ws_bytes, void *stream);
+
+/*
  * ldlt_rpm_trss -- Algorithm 1 (TRSS) of Section 4, Problem 1: the upper
  * triangular X with X^T U + U^T X = C over Z/pZ, the routine Algorithm 3
  * uses to eliminate the leading block of Q C Q^T with the pivots of B.

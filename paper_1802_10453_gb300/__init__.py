@@ -29,6 +29,8 @@ from .binding import (  # noqa: F401
     factor,
     factor_raw,
     factor_noalloc,
+    factor_given,
+    given_workspace_bytes,
     factor_batched,
     batched_workspace_bytes,
     set_batched_schedule,

@@ -35,7 +35,8 @@ NOALLOC_BYTES = 48 << 20
 EXPORTS = ["ldlt_rpm_workspace_bytes", "ldlt_rpm_factor", "rpm_from_factor", "ldlt_rpm_version",
            "ldlt_rpm_set_wait_budget_ns", "ldlt_rpm_set_speculation", "ldlt_rpm_factor_noalloc",
            "ldlt_rpm_factor_batched", "ldlt_rpm_batched_workspace_bytes", "ldlt_rpm_batched_set_schedule",
-           "ldlt_rpm_strict", "ldlt_rpm_solve", "ldlt_rpm_trss"]
+           "ldlt_rpm_strict", "ldlt_rpm_solve", "ldlt_rpm_trss", "ldlt_rpm_factor_given",
+           "ldlt_rpm_given_workspace_bytes"]
 BATCH_MAX_N = 512  # LDLT_BATCH_MAX_N
 
 
@@ -71,6 +72,11 @@ def lib():
             L.ldlt_rpm_factor_noalloc.restype = ctypes.c_int
             L.ldlt_rpm_factor_noalloc.argtypes = [c_i64, c_u32, c_vp, c_i64, c_vp, c_vp, c_vp, c_vp,
                                                   ctypes.c_int, c_vp]
+            L.ldlt_rpm_factor_given.restype = ctypes.c_int
+            L.ldlt_rpm_factor_given.argtypes = [c_i64, c_u32, c_vp, c_i64, c_vp, c_vp, c_vp, c_vp,
+                                                ctypes.c_int, c_vp, c_sz, c_vp]
+            L.ldlt_rpm_given_workspace_bytes.restype = ctypes.c_int
+            L.ldlt_rpm_given_workspace_bytes.argtypes = [c_i64, c_u32, ctypes.c_int, ctypes.POINTER(c_sz)]
             L.ldlt_rpm_factor_batched.restype = ctypes.c_int
             L.ldlt_rpm_factor_batched.argtypes = [c_i64, c_vp, c_u32, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp,
                                                   ctypes.c_int, c_vp, c_sz, c_vp]
@@ -169,6 +175,54 @@ def factor(A, p: int, path: int = PATH_TC, stream=None, workspace=None, check: b
     if rc != LDLT_OK:
         raise LdltError(rc, "ldlt_rpm_factor")
     res = dict(perm=perm, e=e, rank=rank, status=status, n=n, p=p)
+    if check:
+        stream.synchronize()
+        st = int(status.item())
+        if st != 0:
+            raise LdltError(st, "device status")
+    return res
+
+
+def given_workspace_bytes(n: int, p: int, path: int = PATH_TC) -> int:
+    out = ctypes.c_size_t(0)
+    rc = lib().ldlt_rpm_given_workspace_bytes(int(n), int(p), int(path), ctypes.byref(out))
+    if rc != LDLT_OK:
+        raise LdltError(rc, "given workspace query")
+    return int(out.value)
+
+
+def factor_given(A, p: int, perm, starts, rank: int, path: int = PATH_TC, stream=None, workspace=None,
+                 check: bool = True) -> dict:
+    """ldlt_rpm_factor_given: L and D of P^T A P = L D L^T for a supplied pivot
+    order `perm` (int sequence or int32 CUDA tensor, perm[k] = original index of
+    position k), 2x2 block starts `starts` (bools, or a tensor whose non-zero
+    entries mark them) and `rank`.  A (square int32 CUDA tensor, lower triangle
+    read) is overwritten like factor() does.  Returns dict(perm, e, rank,
+    status, n, p); with check=True raises if the device status is non-zero
+    (LDLT_ERR_INCONSISTENT: the structure does not fit A)."""
+    import torch
+    if not A.is_cuda or A.dtype != torch.int32 or A.dim() != 2 or A.shape[0] != A.shape[1]:
+        raise LdltError(LDLT_ERR_ARG, "A must be a square int32 CUDA tensor")
+    n = A.shape[0]
+    if n > 0 and A.stride(1) != 1:
+        raise LdltError(LDLT_ERR_ARG, "rows of A must be contiguous")
+    dev = A.device
+    pt = torch.as_tensor(perm, dtype=torch.int32).to(dev).contiguous().clone()
+    et = (torch.as_tensor(starts).to(dev) != 0).to(torch.int32).contiguous()
+    if pt.numel() != n or et.numel() != n:
+        raise LdltError(LDLT_ERR_ARG, "perm and starts need n entries")
+    rk = torch.tensor([int(rank)], dtype=torch.int64, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    nbytes = given_workspace_bytes(n, p, path)
+    ws = workspace if workspace is not None else _workspace(nbytes, dev)
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    lda = A.stride(0) if n > 0 else 1
+    rc = lib().ldlt_rpm_factor_given(n, int(p), A.data_ptr(), lda, pt.data_ptr(), et.data_ptr(), rk.data_ptr(),
+                                     status.data_ptr(), int(path), ws.data_ptr(), ws.numel(), stream.cuda_stream)
+    if rc != LDLT_OK:
+        raise LdltError(rc, "ldlt_rpm_factor_given")
+    res = dict(perm=pt, e=et, rank=rk, status=status, n=n, p=p)
     if check:
         stream.synchronize()
         st = int(status.item())

@@ -23,7 +23,7 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path
 LIBS = {
     "libldlt_rpm.so": ["panel.cu", "kernels_misc.cu", "syrdk_fp64.cu", "syrdk_tc.cu", "ldlt_rpm.cu",
                        "noalloc.cu", "batched.cu", "strict_char2.cu",
-                       "solve.cu", "trss.cu"],
+                       "solve.cu", "trss.cu", "given.cu"],
     "libldlt_gen.so": ["gen_kernels.cu"],
 }
 HEADERS = ["field.cuh", "ldlt_internal.cuh"]

@@ -22,6 +22,30 @@ __global__ void ingest_kernel(const uint32_t *__restrict__ A, int64_t lda, int64
     }
 }
 
+// The same for a supplied order: S[i][j] = A[perm[i]][perm[j]] mod p, read
+// from A's lower triangle (the symmetric entry).  An index outside [0, n) sets
+// *bad and is not read.
+__global__ void ingest_perm_kernel(const uint32_t *__restrict__ A, int64_t lda, int64_t n,
+                                   const int32_t *__restrict__ perm, uint32_t *__restrict__ S, int64_t ldS,
+                                   int *__restrict__ idx, FieldP f, int *bad)
+{
+    const int64_t i = blockIdx.y;
+    if (i >= n) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) idx[i] = (int)i;
+    const int64_t a = perm[i];
+    uint32_t *dst = S + i * ldS;
+    const bool ra = a >= 0 && a < n;
+    if (!ra && blockIdx.x == 0 && threadIdx.x == 0) atomicExch(bad, 1);
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j <= i;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = perm[j];
+        uint32_t v = 0u;
+        if (ra && b >= 0 && b < n) v = a >= b ? __ldg(A + a * lda + b) : __ldg(A + b * lda + a);
+        else atomicExch(bad, 1);
+        dst[j] = v >= f.p ? v % f.p : v;
+    }
+}
+
 // Lw[idx[t]][col0 + j] = LpT[j][t]: transpose through shared memory so both
 // the reads (along t) and the writes (along j) are coalesced.
 __global__ void lw_scatter_kernel(const uint32_t *__restrict__ LpT, int64_t ldL, int m, int np,
@@ -145,6 +169,15 @@ cudaError_t launch_ingest(const uint32_t *A, int64_t lda, int64_t n, uint32_t *S
     if (n == 0) return cudaSuccess;
     dim3 grid(gx_for(n, 256), (unsigned)n);
     ingest_kernel<<<grid, 256, 0, st>>>(A, lda, n, S, ldS, idx, f);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ingest_perm(const uint32_t *A, int64_t lda, int64_t n, const int32_t *perm, uint32_t *S,
+                               int64_t ldS, int *idx, FieldP f, int *bad, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    dim3 grid(gx_for(n, 256), (unsigned)n);
+    ingest_perm_kernel<<<grid, 256, 0, st>>>(A, lda, n, perm, S, ldS, idx, f, bad);
     return cudaGetLastError();
 }
 

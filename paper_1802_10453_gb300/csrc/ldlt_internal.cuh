@@ -99,6 +99,13 @@ struct PanelParams {
 // ---- launchers (host) -------------------------------------------------------
 cudaError_t launch_ingest(const uint32_t *A, int64_t lda, int64_t n, uint32_t *S, int64_t ldS,
                           int *idx, FieldP f, cudaStream_t st);
+cudaError_t launch_ingest_perm(const uint32_t *A, int64_t lda, int64_t n, const int32_t *perm, uint32_t *S,
+                               int64_t ldS, int *idx, FieldP f, int *bad, cudaStream_t st);
+// ldlt_rpm_factor's body; with gperm != NULL it factors P^T A P for that
+// order (perm[k] = original index of position k), flagging a bad index in *gbad
+int factor_core(int64_t n, uint32_t p, uint32_t *A, int64_t lda, int32_t *perm, uint32_t *e, int64_t *rank,
+                int32_t *status, int path, void *ws, size_t ws_bytes, void *stream, const int32_t *gperm,
+                int *gbad);
 cudaError_t launch_panel(const PanelParams &pp, int grid, cudaStream_t st);
 cudaError_t launch_lw_scatter(const uint32_t *LpT, int64_t ldL, int m, int np, const int *idx,
                               uint32_t *Lw, int64_t ldw, int col0, cudaStream_t st);

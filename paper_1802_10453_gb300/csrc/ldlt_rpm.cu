@@ -220,6 +220,13 @@ extern "C" int ldlt_rpm_factor(int64_t n, uint32_t p, uint32_t *A, int64_t lda, 
                                uint32_t *e, int64_t *rank, int32_t *status, int path, void *ws,
                                size_t ws_bytes, void *stream)
 {
+    return factor_core(n, p, A, lda, perm, e, rank, status, path, ws, ws_bytes, stream, nullptr, nullptr);
+}
+
+int factor_core(int64_t n, uint32_t p, uint32_t *A, int64_t lda, int32_t *perm, uint32_t *e, int64_t *rank,
+                int32_t *status, int path, void *ws, size_t ws_bytes, void *stream, const int32_t *gperm,
+                int *gbad)
+{
     int rc = check_args(n, p, path);
     if (rc != LDLT_OK) return rc;
     if (!rank || !status) return LDLT_ERR_ARG;
@@ -261,7 +268,8 @@ extern "C" int ldlt_rpm_factor(int64_t n, uint32_t p, uint32_t *A, int64_t lda, 
     const FieldP f = make_field(p);
     const int limbs = (path == LDLT_PATH_TC) ? tc_limbs(p) : 0;
 
-    CK(launch_ingest(A, lda, n, Sbuf[0], ldS, idxb[0], f, st));
+    if (gperm) CK(launch_ingest_perm(A, lda, n, gperm, Sbuf[0], ldS, idxb[0], f, gbad, st));
+    else CK(launch_ingest(A, lda, n, Sbuf[0], ldS, idxb[0], f, st));
     const bool prof = g_prof.on;
     if (prof) g_prof.acc[5] += 1;
 
