@@ -529,6 +529,28 @@ def main():
         given_line = {"ms": ms_gv, "value": ops / (ms_gv * 1e-3) / 1e9, "unit": UNIT,
                       "status": int(gres["status"].item()),
                       "form": "P^T A P gathered in the ingest pass, same GPU path, structure checked"}
+        # the order of the recursive Algorithms 2/3, read off R_A on the host,
+        # then the given-P mode in that order
+        t0 = time.perf_counter()
+        rpm_h = lr.rpm_from_factor(res).cpu().tolist()
+        rperm, rstarts, rrank = lr.recursive_order(rpm_h)
+        host_ms = (time.perf_counter() - t0) * 1e3
+        ms_r = []
+        for it in range(3):
+            A.copy_(A0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rres = lr.factor_given(A, p, rperm, rstarts, rrank, stream=stream, workspace=wsg, check=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if it:
+                ms_r.append(e0.elapsed_time(e1))
+        given_line["recursive_order"] = {"ms": statistics.median(ms_r), "host_order_ms": host_ms,
+                                         "status": int(rres["status"].item()),
+                                         "rpm_equals_planted": bool(
+                                             (lr.rpm_from_factor(rres).cpu().numpy() == partner).all())
+                                         if partner is not None else None}
         del wsg
 
     # Algorithm 1 (TRSS): X^T U + U^T X = C at n = 4096 over the paper's 23-bit prime

@@ -30,6 +30,7 @@ from .binding import (  # noqa: F401
     factor_raw,
     factor_noalloc,
     factor_given,
+    factor_recursive,
     given_workspace_bytes,
     factor_batched,
     batched_workspace_bytes,
@@ -46,3 +47,4 @@ from .binding import (  # noqa: F401
     effective_ops,
 )
 from .tune import OnlineTuner, tune_batched  # noqa: E402,F401
+from .recursive_order import recursive_order  # noqa: E402,F401

@@ -231,6 +231,25 @@ def factor_given(A, p: int, perm, starts, rank: int, path: int = PATH_TC, stream
     return res
 
 
+def factor_recursive(A, p: int, path: int = PATH_TC, stream=None, check: bool = True) -> dict:
+    """The factorisation the recursive Algorithms 2/3 compute (Section 4): their
+    pivot order and block structure, with its unique L and D (odd p; p = 2 with
+    in-block entry 0), in place in A like factor().
+
+    Their order follows from R_A alone (recursive_order.py): one factor()
+    pass on a copy of A gives R_A, the host derives the order, and
+    factor_given() computes that factorisation.  Returns the factor_given
+    result dict (perm, e, rank, status, n, p)."""
+    import torch
+    from .recursive_order import recursive_order
+    A0 = A.clone()
+    first = factor(A0, p, path=path, stream=stream, check=check)
+    rpm = rpm_from_factor(first, stream=stream).cpu().tolist()
+    del A0
+    perm, starts, rank = recursive_order(rpm)
+    return factor_given(A, p, perm, starts, rank, path=path, stream=stream, check=check)
+
+
 def factor_noalloc(A, p: int, perm, e, rank, status, path: int = PATH_TC, stream=None) -> dict:
     """ldlt_rpm_factor_noalloc: factor A in place like factor(), with the
     library's own fixed scratch array instead of a workspace, for callers that

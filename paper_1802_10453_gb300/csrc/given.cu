@@ -66,12 +66,14 @@ __global__ void gv_finish_kernel(int64_t n, int32_t *perm, const uint32_t *e, co
                                  const int32_t *psave, const uint8_t *emark, const int *flags, int32_t *status)
 {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool badperm = flags[0] != 0;  // reported alone: the order was not a permutation
     if (k == 0) {
-        if (flags[0]) atomicCAS(status, 0, LDLT_ERR_ARG);
+        if (badperm) atomicCAS(status, 0, LDLT_ERR_ARG);
         else if (*rank != reinterpret_cast<const int64_t *>(flags)[1]) atomicCAS(status, 0, LDLT_ERR_INCONSISTENT);
     }
     if (k >= n) return;
-    if (perm[k] != (int32_t)k || (uint8_t)(e[k] != 0u) != emark[k]) atomicCAS(status, 0, LDLT_ERR_INCONSISTENT);
+    if (!badperm && (perm[k] != (int32_t)k || (uint8_t)(e[k] != 0u) != emark[k]))
+        atomicCAS(status, 0, LDLT_ERR_INCONSISTENT);
     perm[k] = psave[k];
 }
 

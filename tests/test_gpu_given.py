@@ -117,3 +117,26 @@ def test_given_n16384_benchmark_structure():
     assert torch.equal(torch.diagonal(A1), torch.diagonal(A2))
     rpm = lr.rpm_from_factor(got).cpu().numpy()
     assert np.array_equal(rpm, partner)
+
+
+@pytest.mark.parametrize("p", [2, 3, 65521, 2147483647])
+@pytest.mark.parametrize("n", [7, 24, 40])
+def test_factor_recursive_matches_the_recursive_oracle(p, n):
+    """The recursion's order read off R_A, then the given-P mode: the GPU
+    returns the factorisation Algorithms 2/3 compute (unique for odd p)."""
+    S = np.tril(_planted(n, p, 77 + 3 * n + p % 7, frac=0.75, pairs=0.4))
+    S = S + np.tril(S, -1).T
+    rec = rc.ldlt_alg2(np.array(S, dtype=object), p)
+    Ad = _lower32(S)
+    res = lr.factor_recursive(Ad, p)
+    M = Ad.cpu().numpy().view(np.uint32).astype(np.int64)
+    L = np.tril(M, -1) + np.eye(n, dtype=np.int64)
+    assert res["perm"].cpu().tolist() == rec["perm"]
+    assert int(res["rank"].item()) == rec["rank"]
+    assert np.array_equal(res["e"].cpu().numpy().view(np.uint32).astype(np.int64), np.array(rec["e"]))
+    if p != 2:
+        assert np.array_equal(L, np.array(rec["L"], dtype=np.int64) % p)
+        assert np.array_equal(np.diag(M), np.array(rec["d"], dtype=np.int64))
+    else:
+        ref = rc.factor_given_p(np.array(S, dtype=object), rec["perm"], [bool(v) for v in rec["e"]], rec["rank"], p)
+        assert np.array_equal(L, np.array(ref["L"], dtype=np.int64))
