@@ -158,7 +158,7 @@ struct Shared {
     volatile int nscan_pub;            // scans published (leader -> watcher warp)
     uint32_t W;
     int np, ia, nzero, nscan, abort, b, owner, nblk;
-    int ph_new, rb, rb_b;              // posted by thread 0: pending head, rollback request
+    int ph_new, rb, rb_b;              // posted by the control warp: pending head, rollback request
     int nrollback;
     long long dbg[16];                 // diagnostics (thread-0 / lane-0 owned slots)
 };

@@ -3,12 +3,15 @@
     python -m paper_1802_10453_gb300.profile_case N [p] [fp64]
     python -m paper_1802_10453_gb300.profile_case WORKLOAD_NAME
     python -m paper_1802_10453_gb300.profile_case batch COUNT
+    python -m paper_1802_10453_gb300.profile_case trss N [p]
 
 The first form draws A = T R T^T (n = N, rank N/2, a quarter of R's non-zeros
 in 2x2 pairs, p = 2^26 - 5 unless given) on the GPU; the second draws the named
 workload of inputs.WORKLOADS exactly as bench.py does; both factor it once
 through the C ABI.  The third draws the first COUNT matrices of the batch
 workload (n in [32, 512], p = 65521) and factors them in one batched call.
+The fourth solves one TRSS (Algorithm 1) of order N (random upper triangular
+U with a non-zero diagonal, random symmetric C; p = 8388593 unless given).
 Prints rank(s) and status.
 """
 import sys
@@ -33,6 +36,18 @@ def main(argv):
         ok = bool((batch.rank[:count].cpu() == torch.from_numpy(rs)).all())
         print("batch", count, "p", p, "ranks as planted", ok)
         return 0 if ok else 1
+    if arg == "trss":
+        n = int(argv[2]) if len(argv) > 2 else 2048
+        p = int(argv[3]) if len(argv) > 3 else 8388593
+        g = torch.Generator(device="cuda")
+        g.manual_seed(1802)
+        U = torch.randint(0, p, (n, n), dtype=torch.int32, device="cuda", generator=g).triu_()
+        U.diagonal().copy_(torch.randint(1, p, (n,), dtype=torch.int32, device="cuda", generator=g))
+        C = torch.randint(0, p, (n, n), dtype=torch.int32, device="cuda", generator=g)
+        st = lr.trss(U, C, p, check=False)
+        torch.cuda.synchronize()
+        print("trss n", n, "p", p, "status", int(st.item()))
+        return 0 if int(st.item()) == 0 else 1
     if arg in inputs.WORKLOADS:
         A, n, _, p, _ = inputs_gpu.workload_matrix(arg)
         path = lr.PATH_TC
