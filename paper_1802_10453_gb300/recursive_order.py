@@ -20,8 +20,6 @@ only, O(n log n).
 """
 from __future__ import annotations
 
-import sys
-
 
 def recursive_order(rpm_col):
     """rpm_col[i] = j where (R_A)_ij = 1, else -1.  Returns (perm, starts,
@@ -32,12 +30,7 @@ def recursive_order(rpm_col):
     for i, j in enumerate(col):
         if j >= n or (j >= 0 and col[j] != i):
             raise ValueError("rpm_col is not a symmetric rook placement")
-    limit = sys.getrecursionlimit()
-    sys.setrecursionlimit(max(limit, 10000))
-    try:
-        blocks, zeros = _alg2(col, list(range(n)))
-    finally:
-        sys.setrecursionlimit(limit)
+    blocks, zeros = _alg2(col, list(range(n)))  # recursion depth about 2 log2(n)
     perm, starts = [], []
     for b in blocks:
         perm += list(b)
