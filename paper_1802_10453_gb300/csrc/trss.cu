@@ -82,8 +82,14 @@ __global__ void __launch_bounds__(TB * TB) trss_diag_kernel(int64_t k0, int nb, 
     if (in) C[(k0 + ty) * ldc + k0 + tx] = c[ty][tx];
 }
 
-// X_k,r for the columns [c0, c0 + TC) of the trailing part: per column j,
-// t = C_k,j - X_kk^T U_k,j, then U_kk^T y = t by forward substitution.
+// X_k,r for the columns [c0, c0 + TC) of the trailing part, one thread per
+// column j: t = C_k,j - X_kk^T U_k,j, then U_kk^T y = t.  Every load is issued
+// first; the TRMM part is nb independent sums; the substitution runs
+// right-looking (y_i final, then subtracted from the later sums), so each of
+// its nb steps costs one reduction and one product on the dependent chain.
+// For p < 2^28 a sum of at most 2 TB products (each < 2^56) stays below 2^63
+// without folding.
+template <bool BIG>
 __global__ void __launch_bounds__(TC) trss_panel_kernel(int64_t k0, int nb, int64_t n, const uint32_t *U,
                                                          int64_t ldu, uint32_t *C, int64_t ldc, FieldP f)
 {
@@ -103,26 +109,34 @@ __global__ void __launch_bounds__(TC) trss_panel_kernel(int64_t k0, int nb, int6
     __syncthreads();
     const int64_t j = k1 + (int64_t)blockIdx.x * TC + threadIdx.x;
     if (j >= n) return;
-    uint32_t uc[TB], y[TB];
+    uint32_t uc[TB], cc[TB];
 #pragma unroll
-    for (int r = 0; r < TB; ++r) uc[r] = r < nb ? rd(U, ldu, k0 + r, j, f) : 0u;
+    for (int r = 0; r < TB; ++r) {
+        uc[r] = r < nb ? rd(U, ldu, k0 + r, j, f) : 0u;
+        cc[r] = r < nb ? rd(C, ldc, k0 + r, j, f) : 0u;
+    }
+    uint64_t acc[TB];
 #pragma unroll
-    for (int i = 0; i < TB; ++i) {
-        if (i >= nb) break;
-        // t_i = c_ij - sum_{k <= i} x_ki u_kj ;  y_i = (t_i - sum_{k < i} u_ki y_k) / u_ii
-        uint64_t acc = 0;
+    for (int i = 0; i < TB; ++i) {  // acc_i = sum_{k <= i} x_ki u_kj (zero rows of x past nb)
+        acc[i] = 0;
 #pragma unroll
-        for (int k = 0; k < TB; ++k) {
-            if (k > i) break;
-            fp_mac(acc, x[k][i], uc[k], f);
-            if (k < i) fp_mac(acc, u[k][i], y[k], f);
+        for (int k = 0; k <= i; ++k) {
+            if (BIG) fp_mac(acc[i], x[k][i], uc[k], f);
+            else acc[i] += (uint64_t)x[k][i] * uc[k];
         }
-        const uint32_t t = fp_sub(rd(C, ldc, k0 + i, j, f), fp_reduce64(acc, f), f);
-        y[i] = fp_mul(t, uinv[i], f);
     }
 #pragma unroll
-    for (int i = 0; i < TB; ++i)
-        if (i < nb) C[(k0 + i) * ldc + j] = y[i];
+    for (int i = 0; i < TB; ++i) {
+        if (i < nb) {
+            const uint32_t y = fp_mul(fp_sub(cc[i], fp_reduce64(acc[i], f), f), uinv[i], f);
+            C[(k0 + i) * ldc + j] = y;
+#pragma unroll
+            for (int l = i + 1; l < TB; ++l) {
+                if (BIG) fp_mac(acc[l], u[i][l], y, f);
+                else acc[l] += (uint64_t)u[i][l] * y;
+            }
+        }
+    }
 }
 
 // C[i][j] -= sum_k (X[k][i] U[k][j] + U[k][i] X[k][j]) for k in the block,
@@ -208,7 +222,10 @@ extern "C" int ldlt_rpm_trss(int64_t n, uint32_t p, const uint32_t *U, int64_t l
         const int64_t rest = n - (k0 + nb);
         if (rest <= 0) continue;
         const unsigned gp = (unsigned)((rest + TC - 1) / TC);
-        trss_panel_kernel<<<gp, TC, 0, st>>>(k0, nb, n, U, ldu, C, ldc, f);
+        if (p >= (1u << 28))
+            trss_panel_kernel<true><<<gp, TC, 0, st>>>(k0, nb, n, U, ldu, C, ldc, f);
+        else
+            trss_panel_kernel<false><<<gp, TC, 0, st>>>(k0, nb, n, U, ldu, C, ldc, f);
         if (p >= (1u << 28))
             trss_syr2k_kernel<true><<<dim3(gp, gp), 256, 0, st>>>(k0, nb, n, U, ldu, C, ldc, f);
         else
