@@ -152,6 +152,32 @@ def cpu_oracle_sample(A_host, p, seconds):
             "seconds": dt}
 
 
+def cpu_one_core(seconds=3.0):
+    """The oracle on one host core: the whole factorisation of the n = 256
+    planted matrix, and a bounded sample (the first pivots, about `seconds`)
+    of the n = 4096 uniform matrix; host-generated inputs of those workloads."""
+    from oracle import oracle as o
+    out = {}
+    A0 = _host_matrix("planted_n256_r192_p65521")
+    t0 = time.perf_counter()
+    r0 = o.ldlt_rpm(A0, 65521, want_L=False, nthreads=1)
+    dt = time.perf_counter() - t0
+    out["planted_n256_r192_p65521"] = {"seconds": dt, "value": effective_ops(256, r0["rank"]) / dt / 1e9,
+                                       "unit": UNIT, "sample": "whole factorisation"}
+    A1 = _host_matrix("uniform_n4096_p8388593")
+    t0 = time.perf_counter()
+    o.ldlt_rpm(A1, 8388593, want_L=False, stop_after=8, nthreads=1)
+    per = max((time.perf_counter() - t0) / 8.0, 1e-4)
+    k = int(max(8, min(4096, seconds / per)))
+    t0 = time.perf_counter()
+    r1 = o.ldlt_rpm(A1, 8388593, want_L=False, stop_after=k, nthreads=1)
+    dt = time.perf_counter() - t0
+    out["uniform_n4096_p8388593"] = {"seconds": dt, "value": r1["ops"] / dt / 1e9, "unit": UNIT,
+                                     "sample": "first %d pivots; ops = sum of m^2 over those steps" % k}
+    out["cores"] = 1
+    return out
+
+
 def profile_traffic(kernel_src):
     """DRAM bytes (read + write) of all SYRDK launches of one factorisation of
     the bench workload, from the committed ncu summary, if it was taken on the
@@ -586,10 +612,12 @@ def main():
         batched = batched_bench(lr, inputs, inputs_gpu, dev, max(3, min(args.steps, 10)))
 
     cpu = None
+    cpu1 = None
     if rank == 0 and world == 1 and not args.no_cpu:
         A_host = np.tril(A0.cpu().numpy()).astype(np.uint32)
         cb = cpu_oracle_sample(A_host, p, args.cpu_seconds)
         cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        cpu1 = cpu_one_core()
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -611,7 +639,8 @@ def main():
             "solve": solve_line,
             "trss": trss_line,
             "given_p": given_line,
-            "cpu_baseline": cpu}
+            "cpu_baseline": cpu,
+            "cpu_one_core": cpu1}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
