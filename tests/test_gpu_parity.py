@@ -348,3 +348,24 @@ def test_strict_is_a_noop_for_odd_p():
     lr.strict(Ad, res)
     torch.cuda.synchronize()
     assert torch.equal(Ad, before[0]) and torch.equal(res["perm"], before[1]) and torch.equal(res["e"], before[2])
+
+
+@pytest.mark.parametrize("n,pad", [(1, 3), (65, 37), (300, 1)])
+def test_padded_rows_lda_above_n_leave_the_padding(n, pad):
+    """A as a view of wider rows (lda = n + pad): the result is the oracle's and
+    the padding (poisoned before the call) is never written."""
+    p = 65521
+    A, _, _ = inputs.planted_matrix(n, (3 * n) // 4, n // 8, p, 55 + n)
+    poison = -559038737  # 0xDEADBEEF as int32
+    buf = torch.full((n, n + pad), poison, dtype=torch.int32, device="cuda")
+    Av = buf[:, :n]
+    Av.copy_(torch.from_numpy(np.tril(np.asarray(A, dtype=np.int64)).astype(np.int32)))
+    res = lr.factor(Av, p)
+    torch.cuda.synchronize()
+    ref = o.ldlt_rpm(A, p)
+    out = Av.cpu().numpy().astype(np.int64)
+    assert int(res["rank"].item()) == ref["rank"]
+    assert np.array_equal(res["perm"].cpu().numpy(), ref["perm"])
+    assert np.array_equal(np.tril(out, -1), np.tril(ref["L"].astype(np.int64), -1))
+    assert np.array_equal(np.diag(out), ref["d"].astype(np.int64))
+    assert bool((buf[:, n:] == poison).all())
