@@ -244,10 +244,13 @@ int ldlt_rpm_strict(int64_t n, uint32_t p, uint32_t *A, int64_t lda,
  *   status   int32[count] (device): 0, or LDLT_ERR_ARG for a matrix whose
  *            n, lda or pointers are invalid (that matrix is left untouched;
  *            the others are factored).
- *   path     LDLT_PATH_FP64 or LDLT_PATH_TC, validated as for
- *            ldlt_rpm_factor.  Matrices of order <= 512 are bound by the
- *            pivot chain, not by the update products, so both values run the
- *            same exact integer arithmetic on the CUDA cores.
+ *   path     LDLT_PATH_FP64 or LDLT_PATH_TC, range-checked as for
+ *            ldlt_rpm_factor (an unknown value, or LDLT_PATH_FP64 with p
+ *            beyond the FP64 range, is an error) but it does not select the
+ *            arithmetic: the batched update's form follows from p alone,
+ *            bf16 limbs on the tensor cores (mma.sync) for p < 2^16 and exact
+ *            64-bit products on the CUDA cores above.  Both give the same
+ *            bits; matrices of order <= 512 are bound by the pivot chain.
  *   ws       device workspace, 256-byte aligned: at least the header plus one
  *            CTA's scratch (1 MiB); ldlt_rpm_batched_workspace_bytes gives the
  *            size that lets every resident CTA run.  A smaller workspace runs
@@ -305,12 +308,16 @@ int ldlt_rpm_batched_set_schedule(int kb, int n_cut, int kb_small);
  *            LDLT_ERR_TOO_LARGE before any device work.
  *   others   exactly as for ldlt_rpm_factor (same outputs, bit for bit).
  *
- * First call on a device: with that device current, the call looks up the
- * array's device address once (cudaGetSymbolAddress) and remembers it for
- * that device; later calls reuse it.  Make that first call before any stream
- * capture begins.  CUDA reserves the array's memory when it loads the module
- * that holds it; with CUDA's default lazy module loading that happens at this
- * first call, not when the library is opened.
+ * Set-up: every call looks up the array's device address on the current
+ * device (cudaGetSymbolAddress, which allocates nothing once the module is
+ * loaded), so the address stays right after cudaDeviceReset or under another
+ * context.  CUDA reserves the array's memory when it loads the module that
+ * holds it; with CUDA's default lazy module loading that happens at the first
+ * call on a device, not when the library is opened.  Make that first call
+ * before any stream capture begins.  A failed lookup returns LDLT_ERR_CUDA
+ * and leaves an error the caller had pending untouched.  Like
+ * ldlt_rpm_factor, the call reads a few words back per panel and so
+ * synchronises `stream`.
  *
  * Every call on a device uses the same array.  The factorisation clears, on
  * the stream, every part of its scratch that must start at zero, so one call
@@ -338,6 +345,26 @@ int ldlt_rpm_version(void);
  * failure-detection tests; 0 restores the default.
  */
 void ldlt_rpm_set_wait_budget_ns(int64_t ns);
+
+/*
+ * ldlt_rpm_test_drop -- failure-detection test hook (no counterpart in the
+ * paper).  Makes the factorisation drop one kind of internal message so that
+ * a bounded device wait is certain to run out, which lets a test check that
+ * the timeout is reported and that the next call is correct.  Nothing faults
+ * or hangs: the wait gives up after the budget of
+ * ldlt_rpm_set_wait_budget_ns, the kernel writes LDLT_ERR_TIMEOUT to *status,
+ * its other CTAs and warps see the abort flag, drain their own in-flight
+ * copies and return, and later kernels of the same call return at once.
+ *   LDLT_TEST_DROP_SCAN_ANSWERS   the pivot chain's helper CTAs never answer
+ *                                 a far scan (tensor or FP64 form);
+ *   LDLT_TEST_DROP_UPDATE_COPIES  the tensor-core SYRDK's copy producer stops
+ *                                 after one pipeline stage (LDLT_PATH_TC).
+ *   0                             normal operation (the default).
+ * Process-wide, not thread-safe.  Returns LDLT_OK or LDLT_ERR_ARG.
+ */
+#define LDLT_TEST_DROP_SCAN_ANSWERS   1
+#define LDLT_TEST_DROP_UPDATE_COPIES  2
+int ldlt_rpm_test_drop(int which);
 
 /*
  * ldlt_rpm_set_speculation -- how many far scans the pivot chain may have in

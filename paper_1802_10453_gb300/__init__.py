@@ -44,6 +44,9 @@ from .binding import (  # noqa: F401
     LDLT_ERR_INCONSISTENT,
     set_wait_budget_ns,
     set_speculation,
+    test_drop,
+    TEST_DROP_SCAN_ANSWERS,
+    TEST_DROP_UPDATE_COPIES,
     effective_ops,
 )
 from .tune import OnlineTuner, tune_batched  # noqa: E402,F401

@@ -36,7 +36,9 @@ EXPORTS = ["ldlt_rpm_workspace_bytes", "ldlt_rpm_factor", "rpm_from_factor", "ld
            "ldlt_rpm_set_wait_budget_ns", "ldlt_rpm_set_speculation", "ldlt_rpm_factor_noalloc",
            "ldlt_rpm_factor_batched", "ldlt_rpm_batched_workspace_bytes", "ldlt_rpm_batched_set_schedule",
            "ldlt_rpm_strict", "ldlt_rpm_solve", "ldlt_rpm_trss", "ldlt_rpm_factor_given",
-           "ldlt_rpm_given_workspace_bytes"]
+           "ldlt_rpm_given_workspace_bytes", "ldlt_rpm_test_drop"]
+TEST_DROP_SCAN_ANSWERS = 1   # LDLT_TEST_DROP_SCAN_ANSWERS
+TEST_DROP_UPDATE_COPIES = 2  # LDLT_TEST_DROP_UPDATE_COPIES
 BATCH_MAX_N = 512  # LDLT_BATCH_MAX_N
 
 
@@ -99,6 +101,8 @@ def lib():
             L.ldlt_rpm_set_wait_budget_ns.argtypes = [c_i64]
             L.ldlt_rpm_set_speculation.restype = ctypes.c_int
             L.ldlt_rpm_set_speculation.argtypes = [ctypes.c_int]
+            L.ldlt_rpm_test_drop.restype = ctypes.c_int
+            L.ldlt_rpm_test_drop.argtypes = [ctypes.c_int]
             _lib = L
     return _lib
 
@@ -119,6 +123,14 @@ def set_speculation(depth: int) -> None:
     rc = lib().ldlt_rpm_set_speculation(int(depth))
     if rc != LDLT_OK:
         raise LdltError(rc, "speculation depth must be in 1..16")
+
+
+def test_drop(which: int) -> None:
+    """Failure-detection test hook (ldlt_rpm_test_drop): drop one kind of
+    internal message so that a bounded device wait runs out (0 = off)."""
+    rc = lib().ldlt_rpm_test_drop(int(which))
+    if rc != LDLT_OK:
+        raise LdltError(rc, "test_drop: 0, TEST_DROP_SCAN_ANSWERS or TEST_DROP_UPDATE_COPIES")
 
 
 def effective_ops(n: int, r: int) -> float:
@@ -257,9 +269,11 @@ def factor_noalloc(A, p: int, perm, e, rank, status, path: int = PATH_TC, stream
 
     The caller supplies the outputs (perm, e: int32[n]; rank: int64[1];
     status: int32[1], all on A's device); this wrapper only passes pointers and
-    neither allocates nor synchronises.  Calls on one device share the scratch
-    array, so calls that overlap in time race; the first call on a device looks
-    up the array's address and should come before any stream capture.
+    allocates nothing (the library call, like factor(), reads a few words back
+    per panel and so synchronises the stream).  Calls on one device share the
+    scratch array, so calls that overlap in time race; the first call on a
+    device loads the module that holds the array and should come before any
+    stream capture.
     Returns dict(perm, e, rank, status, n, p); read status after the stream.
     """
     import torch

@@ -7,19 +7,35 @@
 namespace {
 
 // S[i][j] = A[i][j] mod p for j <= i (lower triangle only); idx = identity.
-__global__ void ingest_kernel(const uint32_t *__restrict__ A, int64_t lda, int64_t n,
-                              uint32_t *__restrict__ S, int64_t ldS, int *__restrict__ idx, FieldP f)
+// One CTA per row.  When every row of A starts on a 16-byte boundary (vec),
+// the row moves in 16-byte chunks (S rows are 256-byte aligned); the chunk
+// that holds the diagonal is written element by element so nothing past it
+// is read or written.
+__device__ __forceinline__ uint32_t red_in(uint32_t v, const FieldP &f) { return v >= f.p ? v % f.p : v; }
+
+__global__ void __launch_bounds__(256) ingest_kernel(const uint32_t *__restrict__ A, int64_t lda, int64_t n,
+                                                     uint32_t *__restrict__ S, int64_t ldS,
+                                                     int *__restrict__ idx, FieldP f, int vec)
 {
-    const int64_t i = blockIdx.y;
+    const int64_t i = blockIdx.x;
     if (i >= n) return;
-    if (blockIdx.x == 0 && threadIdx.x == 0) idx[i] = (int)i;
+    if (threadIdx.x == 0) idx[i] = (int)i;
     const uint32_t *src = A + i * lda;
     uint32_t *dst = S + i * ldS;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j <= i;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t v = __ldg(src + j);
-        dst[j] = v >= f.p ? v % f.p : v;
+    const int64_t len = i + 1;
+    int64_t j0 = 0;
+    if (vec) {
+        const int64_t nfull = len >> 2;  // chunks entirely at or left of the diagonal
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+        uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+        for (int64_t c = threadIdx.x; c < nfull; c += blockDim.x) {
+            uint4 v = __ldg(s4 + c);
+            v.x = red_in(v.x, f); v.y = red_in(v.y, f); v.z = red_in(v.z, f); v.w = red_in(v.w, f);
+            d4[c] = v;
+        }
+        j0 = nfull << 2;
     }
+    for (int64_t j = j0 + threadIdx.x; j < len; j += blockDim.x) dst[j] = red_in(__ldg(src + j), f);
 }
 
 // The same for a supplied order: S[i][j] = A[perm[i]][perm[j]] mod p, read
@@ -100,19 +116,23 @@ __global__ void record_panel_kernel(const PanelOut *__restrict__ out, const int 
 // Final output (PERM of Algorithm 2 applied to L): row k of the result is the
 // L row of original row perm[k].  Strictly lower part: L (columns >= r are
 // identity columns, so zero there; a non-pivot row is zero in every column
-// created after it was found zero); diagonal: D_kk.
-__global__ void finalize_kernel(int64_t n, const uint32_t *__restrict__ Lw, int64_t ldw,
-                                const int *__restrict__ piv_all, const uint32_t *__restrict__ d_all,
-                                const uint32_t *__restrict__ e_all, const int *__restrict__ zero_all,
-                                const int *__restrict__ zero_cols,
-                                int r, uint32_t *__restrict__ A, int64_t lda,
-                                int32_t *__restrict__ perm, uint32_t *__restrict__ e,
-                                int64_t *__restrict__ rank)
+// created after it was found zero); diagonal: D_kk.  One CTA per row; with
+// 16-byte aligned rows of A (vec) the row moves in 16-byte chunks (Lw rows are
+// 256-byte aligned), the chunk that holds the diagonal element by element.
+__global__ void __launch_bounds__(256) finalize_kernel(int64_t n, const uint32_t *__restrict__ Lw, int64_t ldw,
+                                                       const int *__restrict__ piv_all,
+                                                       const uint32_t *__restrict__ d_all,
+                                                       const uint32_t *__restrict__ e_all,
+                                                       const int *__restrict__ zero_all,
+                                                       const int *__restrict__ zero_cols, int r,
+                                                       uint32_t *__restrict__ A, int64_t lda,
+                                                       int32_t *__restrict__ perm, uint32_t *__restrict__ e,
+                                                       int64_t *__restrict__ rank, int vec)
 {
-    const int64_t k = blockIdx.y;
+    const int64_t k = blockIdx.x;
     if (k >= n) return;
     const int src = (k < r) ? piv_all[k] : zero_all[k - r];
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (threadIdx.x == 0) {
         perm[k] = src;
         e[k] = (k < r) ? e_all[k] : 0u;
         if (k == 0) *rank = r;
@@ -120,11 +140,31 @@ __global__ void finalize_kernel(int64_t n, const uint32_t *__restrict__ Lw, int6
     const uint32_t *lrow = Lw + (int64_t)src * ldw;
     uint32_t *arow = A + k * lda;
     const int64_t cmax = (k < r) ? k : (int64_t)zero_cols[k - r];
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c <= k;
-         c += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t dk = (k < r) ? d_all[k] : 0u;
+    int64_t c0 = 0;
+    if (vec) {
+        const int64_t nfull = k >> 2;  // chunks strictly left of the diagonal
+        const uint4 *l4 = reinterpret_cast<const uint4 *>(lrow);
+        uint4 *a4 = reinterpret_cast<uint4 *>(arow);
+        for (int64_t q = threadIdx.x; q < nfull; q += blockDim.x) {
+            const int64_t c = q << 2;
+            uint4 v;
+            if (c + 3 < cmax) {
+                v = __ldg(l4 + q);
+            } else {
+                v.x = c < cmax ? __ldg(lrow + c) : 0u;
+                v.y = c + 1 < cmax ? __ldg(lrow + c + 1) : 0u;
+                v.z = c + 2 < cmax ? __ldg(lrow + c + 2) : 0u;
+                v.w = 0u;  // c + 3 >= cmax
+            }
+            a4[q] = v;
+        }
+        c0 = nfull << 2;
+    }
+    for (int64_t c = c0 + threadIdx.x; c <= k; c += blockDim.x) {
         uint32_t v;
-        if (c == k) v = (k < r) ? d_all[k] : 0u;
-        else if (c < cmax) v = lrow[c];
+        if (c == k) v = dk;
+        else if (c < cmax) v = __ldg(lrow + c);
         else v = 0u;
         arow[c] = v;
     }
@@ -167,8 +207,8 @@ cudaError_t launch_ingest(const uint32_t *A, int64_t lda, int64_t n, uint32_t *S
                           int *idx, FieldP f, cudaStream_t st)
 {
     if (n == 0) return cudaSuccess;
-    dim3 grid(gx_for(n, 256), (unsigned)n);
-    ingest_kernel<<<grid, 256, 0, st>>>(A, lda, n, S, ldS, idx, f);
+    const int vec = ((uintptr_t)A % 16 == 0) && (lda % 4 == 0);
+    ingest_kernel<<<(unsigned)n, 256, 0, st>>>(A, lda, n, S, ldS, idx, f, vec);
     return cudaGetLastError();
 }
 
@@ -213,9 +253,9 @@ cudaError_t launch_finalize(int64_t n, const uint32_t *Lw, int64_t ldw, const in
                             uint32_t *e, int64_t *rank, cudaStream_t st)
 {
     if (n == 0) return cudaSuccess;
-    dim3 grid(gx_for(n, 256), (unsigned)n);
-    finalize_kernel<<<grid, 256, 0, st>>>(n, Lw, ldw, piv_all, d_all, e_all, zero_all, zero_cols, r,
-                                          A, lda, perm, e, rank);
+    const int vec = ((uintptr_t)A % 16 == 0) && (lda % 4 == 0) && (ldw % 4 == 0);
+    finalize_kernel<<<(unsigned)n, 256, 0, st>>>(n, Lw, ldw, piv_all, d_all, e_all, zero_all, zero_cols, r,
+                                                 A, lda, perm, e, rank, vec);
     return cudaGetLastError();
 }
 

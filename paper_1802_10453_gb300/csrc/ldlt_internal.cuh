@@ -94,6 +94,7 @@ struct PanelParams {
     int64_t budget_ns;
     int32_t *status;
     int npend;              // speculative far scans allowed in flight (1..16)
+    int test_drop;          // LDLT_TEST_DROP_SCAN_ANSWERS: helpers never answer a far scan
 };
 
 // ---- launchers (host) -------------------------------------------------------
@@ -141,4 +142,4 @@ cudaError_t launch_split_tc(const uint32_t *LpT, int64_t ldL, const int *sigma, 
 cudaError_t launch_syrdk_tc(const uint32_t *S, int64_t ldS, const int *sigma, int m_next,
                             const void *Aop, const void *Bop, int limbs, int kpad, FieldP f,
                             uint32_t *Snext, int64_t budget_ns, int32_t *status, int num_sms,
-                            cudaStream_t st);
+                            int test_drop, cudaStream_t st);

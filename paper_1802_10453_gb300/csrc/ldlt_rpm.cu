@@ -22,6 +22,7 @@ namespace {
 
 int64_t g_budget_ns = 2000000000LL;
 int g_npend = 16;  // speculative far scans in flight (tunable; LDLT_NPEND)
+int g_test_drop = 0;  // failure-detection tests: LDLT_TEST_DROP_*
 
 // ---- profiling (optional) --------------------------------------------------
 struct Prof {
@@ -205,6 +206,14 @@ extern "C" int ldlt_rpm_set_speculation(int depth)
     return LDLT_OK;
 }
 
+extern "C" int ldlt_rpm_test_drop(int which)
+{
+    if (which != 0 && which != LDLT_TEST_DROP_SCAN_ANSWERS && which != LDLT_TEST_DROP_UPDATE_COPIES)
+        return LDLT_ERR_ARG;
+    g_test_drop = which;
+    return LDLT_OK;
+}
+
 extern "C" int ldlt_rpm_workspace_bytes(int64_t n, uint32_t p, int path, size_t *bytes)
 {
     if (!bytes) return LDLT_ERR_ARG;
@@ -290,6 +299,7 @@ int factor_core(int64_t n, uint32_t p, uint32_t *A, int64_t lda, int32_t *perm, 
         pp.scans = (ScanSlot *)(w + Lo.scans); pp.partner_lp = (uint32_t *)(w + Lo.partner_lp);
         pp.budget_ns = g_budget_ns; pp.status = status;
         pp.npend = g_npend;
+        pp.test_drop = g_test_drop;
         int grid = 1;
         if (m > pp.w) {
             // spread the far rows over every SM, at least MIN_HELPER_ROWS rows per helper
@@ -338,7 +348,8 @@ int factor_core(int64_t n, uint32_t p, uint32_t *A, int64_t lda, int32_t *perm, 
                     if (prof) CK(cudaEventRecord(ev[2], st));
                     upd = true;
                     CK(launch_syrdk_tc(Sbuf[cur], ldS, sigma, m_next, opA, opB, limbs, kpad, f,
-                                       Sbuf[cur ^ 1], g_budget_ns, status, nsm, st));
+                                       Sbuf[cur ^ 1], g_budget_ns, status, nsm,
+                                       g_test_drop == LDLT_TEST_DROP_UPDATE_COPIES, st));
                 }
             } else {
                 CK(launch_compact_copy(Sbuf[cur], ldS, sigma, m_next, Sbuf[cur ^ 1], st));

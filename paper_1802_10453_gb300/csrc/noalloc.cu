@@ -8,32 +8,26 @@
 // launches; only the origin of the scratch pointer differs.
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "../../include/ldlt_rpm.h"
 
 static __device__ __align__(256) unsigned char g_noalloc_ws[LDLT_NOALLOC_BYTES];
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mu;
-void *g_noalloc_ptr[kMaxDevices] = {};
-
-// Device address of g_noalloc_ws on the current device, looked up once per
-// device; nullptr if the lookup fails.
-void *noalloc_scratch(int dev)
+// Device address of g_noalloc_ws on the current device, looked up on every
+// call (the lookup allocates nothing once the module is loaded, and a fresh
+// lookup stays right after cudaDeviceReset or under another context);
+// nullptr if the lookup fails.  A failed lookup clears only the error it
+// raised itself: an error the caller had pending before the call stays.
+void *noalloc_scratch()
 {
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void *ptr = nullptr;
-        if (cudaGetSymbolAddress(&ptr, g_noalloc_ws) != cudaSuccess) {
-            (void)cudaGetLastError();  // leave no pending error behind for the caller
-            return nullptr;
-        }
-        g_noalloc_ptr[dev] = ptr;
+    const bool clean_before = cudaPeekAtLastError() == cudaSuccess;
+    void *ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_ws) != cudaSuccess) {
+        if (clean_before) (void)cudaGetLastError();
+        return nullptr;
     }
-    return g_noalloc_ptr[dev];
+    return ptr;
 }
 
 }  // namespace
@@ -46,10 +40,7 @@ extern "C" int ldlt_rpm_factor_noalloc(int64_t n, uint32_t p, uint32_t *A, int64
     const int rc = ldlt_rpm_workspace_bytes(n, p, path, &need);  // n, p and path checks
     if (rc != LDLT_OK) return rc;
     if (n > LDLT_NOALLOC_MAX_N || need > sizeof(g_noalloc_ws)) return LDLT_ERR_TOO_LARGE;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return LDLT_ERR_CUDA;
-    if (dev < 0 || dev >= kMaxDevices) return LDLT_ERR_NO_DEVICE;
-    void *ws = noalloc_scratch(dev);
+    void *ws = noalloc_scratch();
     if (!ws) return LDLT_ERR_CUDA;
     return ldlt_rpm_factor(n, p, A, lda, perm, e, rank, status, path, ws, sizeof(g_noalloc_ws), stream);
 }

@@ -468,7 +468,7 @@ __device__ void helper_cta(const PanelParams &P, Shared &sh, int lo, int hi)
                 if (valid && c != 0 && t < firstnz) firstnz = t;
             }
         }
-        if (kind == EV_SCAN) {
+        if (kind == EV_SCAN && P.test_drop != 1) {
             for (int o = 16; o > 0; o >>= 1) firstnz = min(firstnz, __shfl_xor_sync(0xffffffffu, firstnz, o));
             if (lane == 0) sh.redi[warp] = firstnz;
             cbar();
@@ -1140,6 +1140,14 @@ __global__ void __launch_bounds__(BLOCK, 1) panel_kernel(PanelParams P)
     extern __shared__ __align__(16) uint8_t smem_raw[];
     Shared &sh = *reinterpret_cast<Shared *>(smem_raw);
     const bool helpers = gridDim.x > 1;
+    if (*(volatile int32_t *)P.status != 0) {
+        // an earlier kernel of this factorisation gave up: end it here
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            P.out->np = 0; P.out->nzero = 0; P.out->iend = 0; P.out->m_next = 0;
+            P.out->abort = 1; P.out->nscan = 0;
+        }
+        return;
+    }
     if (blockIdx.x == 0) {
         leader_cta<BIG>(P, sh, helpers);
     } else {

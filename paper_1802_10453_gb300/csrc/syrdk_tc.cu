@@ -221,6 +221,7 @@ struct TcArgs {
     uint32_t *Snext;
     int64_t budget_ns;
     int32_t *status;
+    int test_drop;                  // LDLT_TEST_DROP_UPDATE_COPIES: producer stops after one stage
     TileMap tm;
     int ntiles;
     int nst;
@@ -278,6 +279,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) syrdk_tc_kernel(const TcArgs ar
                 const __nv_bfloat16 *bblk = args.Bop + (int64_t)J * np_ * args.kprime;
                 for (int s = 0; s < nk; ++s, ++it) {
                     const uint32_t slot = it % NST, ph = (it / NST) & 1u;
+                    if (args.test_drop && it >= 1) {
+                        // failure-detection test: the copies of every later stage are
+                        // withheld, so the MMA issuer's bounded wait must run out
+                        ok = false;
+                        break;
+                    }
                     if (!mbar_wait(smem_u32(&bars[NST + slot]), ph ^ 1u, args.budget_ns, abort_flag)) {
                         ok = false;
                         break;
@@ -289,7 +296,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) syrdk_tc_kernel(const TcArgs ar
                     bulk_g2s(smem_u32(dst + STAGE_A), bblk + (int64_t)s * KST * np_, stageB_bytes, full);
                 }
             }
-            if (!ok) {
+            if (!ok && !args.test_drop) {
                 atomicExch(args.status, LDLT_ERR_TIMEOUT_CODE);
                 *abort_flag = 1;
             }
@@ -631,7 +638,8 @@ cudaError_t launch_split_tc(const uint32_t *LpT, int64_t ldL, const int *sigma, 
 
 cudaError_t launch_syrdk_tc(const uint32_t *S, int64_t ldS, const int *sigma, int m_next, const void *Aop,
                             const void *Bop, int limbs, int kpad, FieldP f, uint32_t *Snext,
-                            int64_t budget_ns, int32_t *status, int num_sms, cudaStream_t st)
+                            int64_t budget_ns, int32_t *status, int num_sms, int test_drop,
+                            cudaStream_t st)
 {
     if (m_next == 0) return cudaSuccess;
     TcArgs a;
@@ -641,7 +649,7 @@ cudaError_t launch_syrdk_tc(const uint32_t *S, int64_t ldS, const int *sigma, in
     a.limbs = limbs; a.bn = tc_bn(limbs); a.nprime = limbs * a.bn; a.kprime = tc_limbs_a(f.p, &ash) * kpad;
     a.f = f;
     a.bias = ((((uint64_t)1 << 50) / f.p) + 1) * (uint64_t)f.p;
-    a.Snext = Snext; a.budget_ns = budget_ns; a.status = status;
+    a.Snext = Snext; a.budget_ns = budget_ns; a.status = status; a.test_drop = test_drop;
     const int nI = (m_next + BM - 1) / BM;
     a.tm.nI = nI;
     a.tm.c = BM / a.bn;

@@ -70,6 +70,14 @@ def test_factor_argument_errors(libs):
     assert L.rpm_from_factor(-1, None, None, None, None, None) == -1
 
 
+def test_test_drop_codes(libs):
+    """The failure-detection hook accepts only its documented codes (host only)."""
+    L = libs.lib()
+    assert L.ldlt_rpm_test_drop(3) == -1
+    assert L.ldlt_rpm_test_drop(-1) == -1
+    assert L.ldlt_rpm_test_drop(0) == 0
+
+
 def test_effective_ops_formula(libs):
     # Section 6: r^3/3 + n^2 r - r^2 n; r = n gives n^3/3
     assert libs.effective_ops(300, 300) == pytest.approx(300 ** 3 / 3)
