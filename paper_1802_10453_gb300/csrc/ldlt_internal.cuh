@@ -14,8 +14,9 @@ constexpr int ROWS_PER_HELPER = 256;  // far rows per helper CTA kept in shared 
 constexpr int MIN_HELPER_ROWS = 64;   // fewer rows than this per helper is not worth a CTA
 constexpr int PANEL_THREADS_V2 = 576; // 16 compute warps (two threads per row) + 2 service warps
 constexpr int MAX_EVENTS = 8192;      // events per panel (a panel ends early at the cap)
-constexpr int MAX_SCANS = 4096;       // far scans per panel
-constexpr int PARTNER_RING = 64;      // per-scan partner-row buffers
+constexpr int MAX_SCANS = 4096;       // far scans per panel (re-issued scans included)
+constexpr int SCAN_RING = 64;         // per-scan buffers (candidate rows, scan columns), by scan id
+constexpr int PSTR = KP_MAX + 8;      // words per candidate row: U~ values, then x~ at KP_MAX
 constexpr int MAX_PANEL_GRID = 256;
 constexpr int EV_WORDS = 4 * KP_MAX;  // payload words per event
 constexpr int EV_REC = 8 + EV_WORDS;  // event record: header (one Event) then payload
@@ -24,17 +25,17 @@ constexpr int EV_REC = 8 + EV_WORDS;  // event record: header (one Event) then p
 // every row starts on a 256-byte boundary.
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
-enum EventKind : int { EV_PIVOT1 = 1, EV_PIVOT2 = 2, EV_SCAN = 3, EV_END = 4 };
+enum EventKind : int { EV_PIVOT1 = 1, EV_PIVOT2 = 2, EV_SCAN = 3, EV_END = 4, EV_FARPAIR = 5 };
 
 // One message from the leader CTA to the helper CTAs (see panel.cu).
 struct Event {
     int kind;
     int a, b;        // compact rows of the pivot (b only for 2x2)
-    int np;          // pivots before this event (length of the z vectors)
+    int np;          // length of the z vectors (storage columns they cover)
     uint32_t s0;     // the scale W of the division-free Crout form
-    uint32_t s1;
-    int scan_id;     // EV_SCAN: sequence number of the scan
-    int pad;
+    int col;         // storage column the event writes (pivots, far pair)
+    int scan_id;     // EV_SCAN: scan id; EV_FARPAIR: the far pair's own scan
+    int aux;         // EV_FARPAIR: corrections | re-issued scans << 16
 };
 
 // Counters the CTAs of one panel launch share (zeroed before the launch).
@@ -55,17 +56,18 @@ struct ScanSlot {
 };
 static_assert(MAX_PANEL_GRID <= 8 * 32, "one answer bit per helper CTA");
 
-// What the panel kernel reports back to the host.
+// What the panel kernel reports back to the host.  Pivots, D and the L
+// columns (LpC) are in pivot order.
 struct PanelOut {
     int np;          // pivots taken in this panel (L columns)
     int nzero;       // non-pivot rows found
     int iend;        // first window row not processed
     int m_next;      // order of the next Schur complement
     int abort;
-    int nscan;       // far scans issued (diagnostics)
+    int nscan;       // far scans issued, re-issued ones included (diagnostics)
     int pad[2];
-    long long cyc[8];       // leader clock64 cycles per phase (diagnostics)
-    long long dbg[16];      // pivot-chain diagnostics (see ldlt_rpm_profile_read)
+    long long cyc[8];       // unused (zero)
+    long long dbg[16];      // pivot-chain counters (see ldlt_rpm_profile_read)
     int piv_rows[KP_MAX];   // compact rows, pivot order
     uint32_t dval[KP_MAX];  // D diagonal
     uint32_t eval[KP_MAX];  // x at a 2x2 block start, else 0
@@ -80,7 +82,8 @@ struct PanelParams {
     FieldP f;
     int kp;                 // pivot budget of this panel (<= KP_MAX)
     int w;                  // window rows min(W0, m)
-    uint32_t *LpT;          // LpT[k * ldL + t]: L entry of compact row t, panel column k
+    uint32_t *LpT;          // LpT[k * ldL + t]: scaled Schur column k (storage order) of compact row t
+    uint32_t *LpC;          // LpC[k * ldL + t]: L entry of compact row t, pivot-order column k (output)
     int64_t ldL;
     uint8_t *consumed;      // [m]: partner rows taken by 2x2 pivots (zeroed)
     const int *idx;         // [m]: original index of compact row
@@ -90,10 +93,11 @@ struct PanelParams {
     PanelSync *sync;
     uint32_t *evlog;        // [MAX_EVENTS][EV_REC] event records
     ScanSlot *scans;        // [MAX_SCANS]
-    uint32_t *partner_lp;   // [PARTNER_RING][MAX_PANEL_GRID][KP_MAX]: candidate rows per scan
+    uint32_t *partner_lp;   // [SCAN_RING][MAX_PANEL_GRID][PSTR]: candidate rows per scan
+    uint32_t *scancol;      // [SCAN_RING][ldL]: scaled far values of each scan's row
     int64_t budget_ns;
     int32_t *status;
-    int npend;              // speculative far scans allowed in flight (1..16)
+    int npend;              // far scans allowed in flight (1..16)
     int test_drop;          // LDLT_TEST_DROP_SCAN_ANSWERS: helpers never answer a far scan
 };
 

@@ -109,8 +109,8 @@ int fp64_kred(uint32_t p)
 
 struct Layout {
     int64_t ldS;
-    size_t S0, S1, Lw, LpT, idx0, idx1, sigma, consumed, piv_all, d_all, e_all, zero_all, zero_cols;
-    size_t out, sync, evlog, scans, partner_lp, opA, opB, total;
+    size_t S0, S1, Lw, LpT, LpC, idx0, idx1, sigma, consumed, piv_all, d_all, e_all, zero_all, zero_cols;
+    size_t out, sync, evlog, scans, partner_lp, scancol, opA, opB, total;
 };
 
 constexpr int MAX_GRID = 1024;
@@ -130,6 +130,7 @@ int make_layout(int64_t n, uint32_t p, int path, Layout &L)
     L.S1 = take(mat);
     L.Lw = take(mat);
     L.LpT = take((size_t)KP_MAX * (size_t)L.ldS * 4);
+    L.LpC = take((size_t)KP_MAX * (size_t)L.ldS * 4);
     L.idx0 = take((size_t)nn * 4);
     L.idx1 = take((size_t)nn * 4);
     L.sigma = take((size_t)nn * 4);
@@ -143,7 +144,8 @@ int make_layout(int64_t n, uint32_t p, int path, Layout &L)
     L.sync = take(sizeof(PanelSync));
     L.evlog = take((size_t)MAX_EVENTS * EV_REC * 4);
     L.scans = take((size_t)MAX_SCANS * sizeof(ScanSlot));
-    L.partner_lp = take((size_t)PARTNER_RING * MAX_PANEL_GRID * KP_MAX * 4);
+    L.partner_lp = take((size_t)SCAN_RING * MAX_PANEL_GRID * PSTR * 4);
+    L.scancol = take((size_t)SCAN_RING * (size_t)L.ldS * 4);
     if (path == LDLT_PATH_FP64) {
         L.opA = take(fp64_operand_bytes(nn));
         L.opB = L.opA;  // GT follows GDT inside the same allocation
@@ -263,6 +265,7 @@ int factor_core(int64_t n, uint32_t p, uint32_t *A, int64_t lda, int32_t *perm, 
     uint32_t *Sbuf[2] = {(uint32_t *)(w + Lo.S0), (uint32_t *)(w + Lo.S1)};
     uint32_t *Lw = (uint32_t *)(w + Lo.Lw);
     uint32_t *LpT = (uint32_t *)(w + Lo.LpT);
+    uint32_t *LpC = (uint32_t *)(w + Lo.LpC);
     int *idxb[2] = {(int *)(w + Lo.idx0), (int *)(w + Lo.idx1)};
     int *sigma = (int *)(w + Lo.sigma);
     uint8_t *consumed = w + Lo.consumed;
@@ -292,11 +295,12 @@ int factor_core(int64_t n, uint32_t p, uint32_t *A, int64_t lda, int32_t *perm, 
         PanelParams pp;
         pp.S = Sbuf[cur]; pp.ldS = ldS; pp.m = m; pp.f = f;
         pp.kp = KP_MAX; pp.w = m < W0 ? m : W0;
-        pp.LpT = LpT; pp.ldL = ldS;
+        pp.LpT = LpT; pp.LpC = LpC; pp.ldL = ldS;
         pp.consumed = consumed; pp.idx = idxb[cur]; pp.sigma = sigma; pp.idx_next = idxb[cur ^ 1];
         pp.out = out; pp.sync = sync;
         pp.evlog = (uint32_t *)(w + Lo.evlog);
         pp.scans = (ScanSlot *)(w + Lo.scans); pp.partner_lp = (uint32_t *)(w + Lo.partner_lp);
+        pp.scancol = (uint32_t *)(w + Lo.scancol);
         pp.budget_ns = g_budget_ns; pp.status = status;
         pp.npend = g_npend;
         pp.test_drop = g_test_drop;
@@ -326,7 +330,7 @@ int factor_core(int64_t n, uint32_t p, uint32_t *A, int64_t lda, int32_t *perm, 
             for (int i = 0; i < 16; ++i) g_prof.acc[16 + i] += (double)rb.dbg[i];
         }
         if (aborted) return LDLT_OK;  // LDLT_ERR_TIMEOUT is in *status
-        CK(launch_lw_scatter(LpT, ldS, m, np, idxb[cur], Lw, ldS, r0, st));
+        CK(launch_lw_scatter(LpC, ldS, m, np, idxb[cur], Lw, ldS, r0, st));
         if (prof && np > 0) g_prof.acc[5] += 1;
         bool upd = false;
         if (m_next > 0) {
@@ -335,7 +339,7 @@ int factor_core(int64_t n, uint32_t p, uint32_t *A, int64_t lda, int32_t *perm, 
                 if (path == LDLT_PATH_FP64) {
                     double *GDT = (double *)(w + Lo.opA);
                     double *GT = GDT + (size_t)KP_MAX * ldS;
-                    CK(launch_split_fp64(LpT, ldS, sigma, m_next, np, out, f, GDT, GT, ldS, kpad, st));
+                    CK(launch_split_fp64(LpC, ldS, sigma, m_next, np, out, f, GDT, GT, ldS, kpad, st));
                     if (prof) CK(cudaEventRecord(ev[2], st));
                     upd = true;
                     CK(launch_syrdk_fp64(Sbuf[cur], ldS, sigma, m_next, GDT, GT, ldS, kpad, f,
@@ -344,7 +348,7 @@ int factor_core(int64_t n, uint32_t p, uint32_t *A, int64_t lda, int32_t *perm, 
                     uint8_t *opA = w + Lo.opA;
                     const size_t aBytes = (size_t)round_up(round_up(n, 128) * (int64_t)limbs * KP_MAX * 2, 256);
                     uint8_t *opB = opA + aBytes;
-                    CK(launch_split_tc(LpT, ldS, sigma, m_next, np, out, f, limbs, kpad, opA, opB, st));
+                    CK(launch_split_tc(LpC, ldS, sigma, m_next, np, out, f, limbs, kpad, opA, opB, st));
                     if (prof) CK(cudaEventRecord(ev[2], st));
                     upd = true;
                     CK(launch_syrdk_tc(Sbuf[cur], ldS, sigma, m_next, opA, opB, limbs, kpad, f,
