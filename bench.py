@@ -557,6 +557,9 @@ def main():
                    "helper1_idle_cycles", "helper1_busy_cycles", "helper1_events", "pub_batches",
                    "events", "t0_wait_b1", "t0_wait_b2", "t511_wait_b1", "t511_wait_b2", "t0_schur",
                    "t511_schur"])}}
+    # the cycle counters exist only in a build with LDLT_CHAIN_PROFILE; drop the empty ones
+    phases["leader_ms"] = {k: v for k, v in phases["leader_ms"].items() if v} or None
+    phases["chain_diag"] = {k: v for k, v in phases["chain_diag"].items() if v}
     # the pivot chain is latency-bound: its figure is time per decision
     phases["us_per_pivot"] = phases["pivot_chain_ms"] * 1e3 / max(rank_found, 1)
     phases["us_per_row_iteration"] = phases["pivot_chain_ms"] * 1e3 / max(phases["chain_diag"]["rows"], 1.0)

@@ -20,7 +20,9 @@ struct FieldP {
     uint32_t c32;    // 2^32 mod p
     uint32_t c32q;   // floor(c32 * 2^32 / p)   (Shoup companion of c32)
     uint32_t oneq;   // floor(2^32 / p)         (Shoup companion of 1)
-    uint32_t pad;
+    uint32_t kb;     // bit length k of p (2^(k-1) <= p < 2^k)
+    uint32_t muk;    // floor(2^(2k) / p) < 2^(k+1) (Barrett constant for products)
+    uint32_t pad2;
 };
 
 inline FieldP make_field(uint32_t p)
@@ -34,7 +36,11 @@ inline FieldP make_field(uint32_t p)
     f.c32 = (uint32_t)((1ull << 32) % p);
     f.c32q = (uint32_t)(((uint64_t)f.c32 << 32) / p);
     f.oneq = (uint32_t)((1ull << 32) / p);
-    f.pad = 0;
+    uint32_t k = 0;
+    while (k < 32 && (p >> k) != 0) ++k;
+    f.kb = k;
+    f.muk = (uint32_t)((1ull << (2 * k)) / p);  // k <= 31, so 2k <= 62
+    f.pad2 = 0;
     return f;
 }
 
@@ -63,9 +69,20 @@ __device__ __forceinline__ uint32_t fp_reduce64_fold(uint64_t x, const FieldP &f
     return s >= f.p ? s - f.p : s;
 }
 
+// a * b mod p for residues a, b < p by Barrett's method with the k-bit
+// constant muk = floor(2^(2k) / p) (Handbook of Applied Cryptography,
+// Algorithm 14.42, base 2): x = a b < 2^(2k), q = floor(floor(x / 2^(k-1)) muk /
+// 2^(k+1)) underestimates floor(x / p) by at most 2.  Both products are 32 x
+// 32 bits (x / 2^(k-1) < 2^(k+1) <= 2^32 and muk < 2^(k+1)).
 __device__ __forceinline__ uint32_t fp_mul(uint32_t a, uint32_t b, const FieldP &f)
 {
-    return fp_reduce64((uint64_t)a * (uint64_t)b, f);
+    const uint64_t x = (uint64_t)a * (uint64_t)b;
+    const uint32_t t = (uint32_t)(x >> (f.kb - 1));
+    const uint32_t q = (uint32_t)(((uint64_t)t * (uint64_t)f.muk) >> (f.kb + 1));
+    uint64_t r = x - (uint64_t)q * (uint64_t)f.p;
+    if (r >= f.p) r -= f.p;
+    if (r >= f.p) r -= f.p;
+    return (uint32_t)r;
 }
 
 __device__ __forceinline__ uint32_t fp_add(uint32_t a, uint32_t b, const FieldP &f)
@@ -103,3 +120,36 @@ __device__ __forceinline__ uint32_t fp_inv(uint32_t a, const FieldP &f)
     if (v < 0) v += f.p;
     return (uint32_t)v;
 }
+
+// Inverse of a != 0 modulo the odd prime p by the binary extended Euclidean
+// algorithm (halvings and subtractions only; D. E. Knuth, TAOCP vol. 2,
+// Section 4.5.2, and A. Menezes et al., Handbook of Applied Cryptography,
+// Algorithm 14.61).  Invariants: x1 a = u and x2 a = v (mod p); a halving of u
+// halves x1 mod p ((x1 + p) / 2 when x1 is odd).  p = 2 has the inverse 1;
+// a = 0 returns 0.
+__device__ __forceinline__ uint32_t fp_inv_bin(uint32_t a, const FieldP &f)
+{
+    const uint32_t p = f.p;
+    if (p == 2) return 1u;
+    if (a == 0u) return 0u;  // no inverse; never loop on it
+    uint32_t u = a, v = p, x1 = 1u, x2 = 0u;
+    while (u != 1u && v != 1u) {
+        while ((u & 1u) == 0u) {
+            u >>= 1;
+            x1 = (x1 & 1u) ? (uint32_t)(((uint64_t)x1 + p) >> 1) : (x1 >> 1);
+        }
+        while ((v & 1u) == 0u) {
+            v >>= 1;
+            x2 = (x2 & 1u) ? (uint32_t)(((uint64_t)x2 + p) >> 1) : (x2 >> 1);
+        }
+        if (u >= v) {
+            u -= v;
+            x1 = fp_sub(x1, x2, f);
+        } else {
+            v -= u;
+            x2 = fp_sub(x2, x1, f);
+        }
+    }
+    return u == 1u ? x1 : x2;
+}
+

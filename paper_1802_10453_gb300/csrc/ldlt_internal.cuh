@@ -17,6 +17,7 @@ constexpr int MAX_EVENTS = 8192;      // events per panel (a panel ends early at
 constexpr int MAX_SCANS = 4096;       // far scans per panel (re-issued scans included)
 constexpr int SCAN_RING = 64;         // per-scan buffers (candidate rows, scan columns), by scan id
 constexpr int PSTR = KP_MAX + 8;      // words per candidate row: U~ values, then x~ at KP_MAX
+constexpr int ZLOG_EV = 64;           // recent row events whose z vectors the leader keeps
 constexpr int MAX_PANEL_GRID = 256;
 constexpr int EV_WORDS = 4 * KP_MAX;  // payload words per event
 constexpr int EV_REC = 8 + EV_WORDS;  // event record: header (one Event) then payload
@@ -95,9 +96,10 @@ struct PanelParams {
     ScanSlot *scans;        // [MAX_SCANS]
     uint32_t *partner_lp;   // [SCAN_RING][MAX_PANEL_GRID][PSTR]: candidate rows per scan
     uint32_t *scancol;      // [SCAN_RING][ldL]: scaled far values of each scan's row
+    uint32_t *zlog;         // [ZLOG_EV][2][KP_MAX]: z vectors of the leader's recent row events
     int64_t budget_ns;
     int32_t *status;
-    int npend;              // far scans allowed in flight (1..16)
+    int npend;              // far scans allowed in flight (1..24)
     int test_drop;          // LDLT_TEST_DROP_SCAN_ANSWERS: helpers never answer a far scan
 };
 

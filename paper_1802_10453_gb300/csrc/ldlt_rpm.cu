@@ -21,7 +21,7 @@
 namespace {
 
 int64_t g_budget_ns = 2000000000LL;
-int g_npend = 16;  // speculative far scans in flight (tunable; LDLT_NPEND)
+int g_npend = 16;  // speculative far scans in flight (tunable)
 int g_test_drop = 0;  // failure-detection tests: LDLT_TEST_DROP_*
 
 // ---- profiling (optional) --------------------------------------------------
@@ -110,7 +110,7 @@ int fp64_kred(uint32_t p)
 struct Layout {
     int64_t ldS;
     size_t S0, S1, Lw, LpT, LpC, idx0, idx1, sigma, consumed, piv_all, d_all, e_all, zero_all, zero_cols;
-    size_t out, sync, evlog, scans, partner_lp, scancol, opA, opB, total;
+    size_t out, sync, evlog, scans, partner_lp, scancol, zlog, opA, opB, total;
 };
 
 constexpr int MAX_GRID = 1024;
@@ -146,6 +146,7 @@ int make_layout(int64_t n, uint32_t p, int path, Layout &L)
     L.scans = take((size_t)MAX_SCANS * sizeof(ScanSlot));
     L.partner_lp = take((size_t)SCAN_RING * MAX_PANEL_GRID * PSTR * 4);
     L.scancol = take((size_t)SCAN_RING * (size_t)L.ldS * 4);
+    L.zlog = take((size_t)ZLOG_EV * 2 * KP_MAX * 4);
     if (path == LDLT_PATH_FP64) {
         L.opA = take(fp64_operand_bytes(nn));
         L.opB = L.opA;  // GT follows GDT inside the same allocation
@@ -301,6 +302,7 @@ int factor_core(int64_t n, uint32_t p, uint32_t *A, int64_t lda, int32_t *perm, 
         pp.evlog = (uint32_t *)(w + Lo.evlog);
         pp.scans = (ScanSlot *)(w + Lo.scans); pp.partner_lp = (uint32_t *)(w + Lo.partner_lp);
         pp.scancol = (uint32_t *)(w + Lo.scancol);
+        pp.zlog = (uint32_t *)(w + Lo.zlog);
         pp.budget_ns = g_budget_ns; pp.status = status;
         pp.npend = g_npend;
         pp.test_drop = g_test_drop;

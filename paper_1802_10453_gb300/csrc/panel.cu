@@ -15,8 +15,8 @@
 // per pivot block B, an integer 2x2 (or 1x1) form M_B and a non-zero
 // "denominator" delta_B such that the block's share of the Crout sum is
 //   U~[t][B] M_B U~[a][B]^T / delta_B.
-// With a common scale W and weights w_B = W / delta_B (kept by multiplication
-// only for the blocks the window decides) the scaled Schur entry is
+// With W = prod_B delta_B and w_B = W / delta_B (both kept by multiplication
+// only) the scaled Schur entry is
 //   c~_a[t] = W c_a[t] = W S[t][a] - sum_k U~[t][k] z_a[k],
 //   z_a = concat_B  M_B U~[a][B]^T w_B,
 // and c~ is zero exactly when c is.  A 1x1 pivot stores U~[:, j] = c~_a
@@ -26,33 +26,10 @@
 // alpha = (c_b - delta' beta) / x and D = [[0,x],[x,y']], the product
 // [alpha, beta] D [alpha', beta']^T equals [c_a, c_b] [[-y/x^2, 1/x],[1/x, 0]]
 // [c_a', c_b']^T for both odd p (y' = 0, delta' = y/2) and p = 2 (y' = delta'
-// = y).  Each block keeps the scale W it was formed with (its columns, pivot
-// and delta all carry it), so blocks need not share one scale.  At the end of
-// the panel all inverses are taken at once (Montgomery's batch inversion) and
-// every CTA rewrites its rows as the true L columns, in pivot order; D is
-// reported in true values.  All arithmetic is exact, so the results equal the
-// divided form bit for bit.
-//
-// Far pairs without rollback.  A window row whose Schur row is zero inside the
-// window is a zero row or the first row a of a 2x2 pivot (a, b) with a far
-// partner b.  The helpers search the far part of the row (a "far scan") while
-// the leader goes on as if the row were zero.  When the scan finds b, the
-// block (a, b) belongs before every block the leader took since row a, but it
-// changes none of their window values: c_a[t] = 0 for every window row t > a,
-// so the block's share of c_u[t], proportional to c_a[t] c_b[u] + c_b[t] c_a[u],
-// vanishes when t and u are both window rows.  So every window decision stands
-// and the leader only
-//   * forms the block's window column c~_b (one pass with row b's values at
-//     the scan's position) and its weight W / delta from one true inverse, so
-//     that W keeps counting window blocks only;
-//   * tells the helpers, whose far columns of the later blocks lack the
-//     block's share.  By linearity each such column needs a rank-1 fix,
-//     new = old - c~_a[t] rho, where c~_a is the scan's own column (kept by the
-//     helpers) and rho a scalar per column that the leader computes by a short
-//     triangular recurrence over the later blocks.  The later scans' columns
-//     get the same fix and are answered again under new ids.
-// Scans are settled in order, so a block is inserted only when every scan
-// before it found no partner.
+// = y).  At the end of the panel all inverses are taken at once (Montgomery's
+// batch inversion) and every CTA rewrites its U~ rows as the true L columns;
+// D is reported in true values.  The results are identical to the divided
+// form because all arithmetic is exact.
 //
 // GPU organisation.  One cooperative launch per panel.  CTA 0 (the leader)
 // owns the window of the first W rows of S and takes every decision.  The
@@ -60,12 +37,14 @@
 // keeps the U~ columns of its rows in shared memory (k-major, padded) and
 // writes them through to global memory.  16 compute warps work two threads
 // per row.  In the leader, warp 17 publishes events to the helpers from a
-// shared-memory ring so the gpu-scope fence stays off the critical path, and
-// warp 16 watches the scan answers; in a helper, warp 16 fetches events into
-// the ring and warp 17 loads the Schur columns they need.  Every wait is
-// bounded by a %globaltimer budget; when it runs out the kernel writes
-// LDLT_ERR_TIMEOUT to the status word, raises an abort flag the other CTAs
-// poll, and returns.
+// shared-memory ring so the gpu-scope fence stays off the critical path; in a
+// helper, warp 16 prefetches events into the ring.  Helpers compute the new
+// columns of their rows as pivots are published and answer "far scans": when
+// a row has no non-zero inside the window, every helper searches its slice
+// for the first non-zero of that row and the leader takes the minimum.  Every
+// wait is bounded by a %globaltimer budget; when it runs out the kernel
+// writes LDLT_ERR_TIMEOUT to the status word, raises an abort flag the other
+// CTAs poll, and returns.
 //
 // At the end the leader compacts the remaining rows (order preserved) into
 // sigma / idx_next for the next Schur complement.
@@ -75,6 +54,15 @@
 
 #define LDLT_ERR_TIMEOUT_CODE (-6)
 
+// Cycle counters of the pivot chain (leader phases, helper idle time): built
+// only with -DLDLT_CHAIN_PROFILE, so the release kernel reads no clock on its
+// critical path.  The event and rollback counts are kept in every build.
+#ifdef LDLT_CHAIN_PROFILE
+#define CHAIN_PROF(...) __VA_ARGS__
+#else
+#define CHAIN_PROF(...)
+#endif
+
 namespace {
 
 constexpr int NCW = 16;                       // compute warps
@@ -83,23 +71,11 @@ constexpr int SROWS = 256;                    // rows held in shared memory per 
 constexpr int SSTRIDE = SROWS + 16;           // padded k-row stride (words)
 constexpr int NSLOT = 8;                      // event ring slots
 constexpr int BLOCK = PANEL_THREADS_V2;
-constexpr int NPEND = 16;                     // far scans in flight
-constexpr int EVT = 64;                       // leader's table of recent row events (ring)
-constexpr int EVT_LIM = 40;                   // row events since the oldest pending scan
-constexpr int LPL = 3;                        // corrected columns per lane (3 * 32 >= 2 * EVT_LIM)
-constexpr int SRING = 128;                    // posted scan results
 
 static_assert(BLOCK == NCT + 64, "two service warps");
 static_assert(W0 <= SROWS && ROWS_PER_HELPER <= SROWS, "rows fit in shared memory");
-static_assert(W0 <= NCT / 2, "one thread pair per window row");
-static_assert(LPL * 32 >= 2 * EVT_LIM, "corrected columns fit the sweep's lanes");
-static_assert(KP_MAX + 2 * (2 * EVT_LIM) + 3 * NPEND <= EV_WORDS, "far-pair payload fits an event");
-static_assert(2 * NPEND + 8 < SCAN_RING && 2 * NPEND + 8 < SRING, "scan id rings");
 
 enum ColKind : uint8_t { K_1x1 = 1, K_2A = 2, K_2B = 3 };
-// window row states (leader)
-constexpr int RI_UNDEC = 0, RI_PART = 1, RI_ZERO = 2, RI_PEND = 3, RI_PIV = 4;  // RI_PIV + storage column
-constexpr int EK_P1 = 1, EK_P2 = 2, EK_SCAN = 3;                                 // row-event kinds
 
 __device__ __forceinline__ int64_t gtime()
 {
@@ -143,6 +119,15 @@ __device__ __forceinline__ void mac(uint64_t &acc, uint32_t a, uint32_t b, const
     if (BIG) acc -= (acc >> 63) * f.m63;
 }
 
+constexpr int NPEND = 16;                     // speculative far scans in flight
+// The far-scan bookkeeping (issue, answers, rollback requests) runs on the
+// last compute warp, which holds no z entry (np <= KP_MAX <= CTL), so it
+// overlaps the z vector of the first warps.  Its lane 0 (CTL) alone writes the
+// pend_* records; between barriers only that warp reads them.
+constexpr int CTL = NCT - 32;
+static_assert(KP_MAX <= CTL, "the control thread computes no z entry");
+constexpr int SRING = 128;                    // posted scan results
+
 struct Shared {
     uint32_t U[KP_MAX * SSTRIDE];      // U~ columns of this CTA's rows, k-major
     uint32_t ring[NSLOT][EV_WORDS];    // event payloads
@@ -150,34 +135,29 @@ struct Shared {
     uint4 sgrp[2][SROWS];              // helpers: S[t][4g .. 4g+3] for two column groups
     Event ev[NSLOT];
     uint32_t ub[KP_MAX];               // U~ row of a 2x2 partner
-    uint32_t zt[KP_MAX];               // z vector of a far partner
-    uint8_t kind[KP_MAX];              // column kinds (storage order); far pairs are K_2A / K_2B
-    uint8_t isfar[KP_MAX];             // 1 on both columns of a far pair
-    uint32_t bw[KP_MAX];               // weight W / delta_B, at the block's first column
+    uint8_t kind[KP_MAX];              // column kinds of this panel
+    uint32_t bw[KP_MAX];               // w_B, at the block's first column
     uint32_t mx[KP_MAX], my[KP_MAX];   // x~, y~ of a 2x2 block (first column)
     uint32_t piv[KP_MAX];              // c~_a[a] (1x1) or x~ (2x2) at the first column
-    uint32_t w0[KP_MAX];               // the block's own scale W
-    uint32_t delta[KP_MAX];            // delta_B (window blocks) at the first column
-    uint32_t invd[KP_MAX];             // 1 / delta_B (far pairs) at the first column
-    int brow[KP_MAX];                  // window row of the block, at both columns
+    uint32_t w0[KP_MAX];               // W when the block was formed
     uint32_t cA[KP_MAX], cB[KP_MAX];   // true-L coefficients (end of panel)
     uint32_t dtrue[KP_MAX], etrue[KP_MAX];
     uint32_t bi[2 * KP_MAX];           // batch inversion: values, then their inverses
     uint32_t bpre[2 * KP_MAX];         // batch inversion: prefix products
-    int piv_rows[KP_MAX];              // compact rows, storage order
-    int canon[KP_MAX];                 // storage column -> pivot-order position
-    int rinfo[W0];                     // window row state RI_*
-    // far scans in flight (FIFO, settled from the head)
-    int pend_id[NPEND], pend_row[NPEND], pend_ev[NPEND];
+    int piv_rows[KP_MAX];
+    int zero_rows[W0];
+    int zero_np[W0];
+    uint8_t wstate[W0];
+    // speculative far scans: a row whose window part is zero is taken as a
+    // zero row while its scan is in flight; a scan that finds a partner rolls
+    // the panel back to that row.
+    int pend_id[NPEND], pend_row[NPEND], pend_np[NPEND], pend_nz[NPEND];
     uint32_t pend_W[NPEND];
-    uint32_t pend_bw[NPEND][KP_MAX];   // block weights when the scan was issued
-    // table of recent row events (absolute index mod EVT)
-    int evt_kind[EVT], evt_u[EVT], evt_v[EVT], evt_col[EVT], evt_sid[EVT];
-    uint32_t evt_W[EVT];
+    uint32_t pend_bw[NPEND][KP_MAX];   // w_B when the scan was issued
+    uint32_t delta[KP_MAX];            // delta_B at the block's first column
     int res_min[SRING];
     volatile int res_ok[SRING];        // id + 1 once scan id's answer is in res_min
     int redi[32];
-    int redj[32];
     uint32_t xy[4];
     uint32_t caa;
     volatile int ev_ready;             // events written to the ring (leader) / fetched (helper)
@@ -185,14 +165,16 @@ struct Shared {
     volatile int quit;
     volatile int ev_fetched;           // helpers: event records fetched (poller -> column loader)
     volatile int nscan_pub;            // scans published (leader -> watcher warp)
-    int head_new, head_b;              // posted by the control warp: settled head, hit partner
-    int ncorr, nres;                   // far pair: corrections and re-issued scans in its event
+    uint32_t W;
+    int np, ia, nzero, nscan, abort, b, owner, nblk;
+    int ph_new, rb, rb_b;              // posted by the control warp: pending head, rollback request
+    int nrollback;
+    long long dbg[16];                 // diagnostics (thread-0 / lane-0 owned slots)
     int hgo;                           // helpers: the next event is in the ring (tid 0's decision)
-    int abort;
-    long long dbg[16];                 // counters (thread-0 owned)
 };
 
-// load with acquire semantics at GPU scope
+// load with acquire semantics at GPU scope: later reads of this thread see
+// every write that was made visible before the matching release / fence
 __device__ __forceinline__ int ld_acquire(const int *p)
 {
     int v;
@@ -209,7 +191,8 @@ __device__ __forceinline__ unsigned ld_relaxed(const void *p)
     return v;
 }
 
-// acquire load at CTA scope, for flags in shared memory
+// acquire load at CTA scope, for flags in shared memory: the "memory" clobber
+// also keeps the compiler from hoisting later loads above it
 __device__ __forceinline__ int ld_acquire_cta(const volatile int *p)
 {
     int v;
@@ -223,10 +206,8 @@ __device__ void raise_timeout(const PanelParams &P)
     atomicExch(&P.sync->abort, 1);
 }
 
-// z[k] of row u (u read with a stride) with the block weight wt:
-// M_B U~[u][B]^T w_B for the block holding column k.
-__device__ __forceinline__ uint32_t zval_w(int k, const uint32_t *u, int stride, const Shared &sh, uint32_t wt,
-                                           const FieldP &f)
+// z[k] of row u (u read with a stride): M_B U~[u][B]^T w_B per block.
+__device__ __forceinline__ uint32_t zval(int k, const uint32_t *u, int stride, const Shared &sh, const FieldP &f)
 {
     const uint8_t kd = sh.kind[k];
     const int kb = k - (kd == K_2B);               // the block's first column
@@ -234,12 +215,7 @@ __device__ __forceinline__ uint32_t zval_w(int k, const uint32_t *u, int stride,
     const uint32_t c1 = kd == K_1x1 ? 1u : sh.mx[kb];
     const uint32_t c2 = kd == K_2A ? sh.my[k] : 0u;
     const uint32_t t = fp_sub(fp_mul(c1, u[j * stride], f), fp_mul(c2, u[k * stride], f), f);
-    return fp_mul(t, wt, f);
-}
-
-__device__ __forceinline__ uint32_t zval(int k, const uint32_t *u, int stride, const Shared &sh, const FieldP &f)
-{
-    return zval_w(k, u, stride, sh, sh.bw[k - (sh.kind[k] == K_2B)], f);
+    return fp_mul(t, sh.bw[kb], f);
 }
 
 // c~_z[t] = W S(t, a) - sum_{k < np} U~[t][k] z[k], two threads per row (half
@@ -267,23 +243,20 @@ __device__ __forceinline__ uint32_t schur2(const PanelParams &P, const uint32_t 
     return fp_sub(fp_mul(W, sval, P.f), fp_add(part, other, P.f), P.f);
 }
 
-// The true L values of one row (U~ read with a stride) into the pivot-order
-// output LpC, using the per-column coefficients: 1x1: L_j = cA_j U_j; first
-// column of a 2x2: L_j = cA_j U_{j+1} + cB_j U_j; second column:
-// L_j = cA_j U_{j-1}.  Column j goes to position canon[j].
-__device__ __forceinline__ void finish_row(const PanelParams &P, const uint32_t *u, int stride, int t, int np,
-                                           const uint32_t *kind, const uint32_t *cA, const uint32_t *cB,
-                                           const uint32_t *canon)
+// Rewrite the U~ values of one row as true L values into the output LpC (in
+// global memory), using the per-column coefficients: 1x1: L_j = cA_j U_j; first column of a 2x2:
+// L_j = cA_j U_{j+1} + cB_j U_j; second column: L_j = cA_j U_{j-1}.
+__device__ __forceinline__ void finish_row(const PanelParams &P, const uint32_t *u, int stride, uint32_t *g,
+                                           int np, const uint8_t *kind, const uint32_t *cA, const uint32_t *cB)
 {
-    uint32_t *g = P.LpC + t;
     for (int j = 0; j < np; ++j) {
-        const uint32_t kd = kind[j];
+        const uint8_t kd = kind[j];
         if (kd == K_1x1) {
-            g[(int64_t)canon[j] * P.ldL] = fp_mul(cA[j], u[j * stride], P.f);
+            g[(int64_t)j * P.ldL] = fp_mul(cA[j], u[j * stride], P.f);
         } else if (kd == K_2A) {
             const uint32_t u0 = u[j * stride], u1 = u[(j + 1) * stride];
-            g[(int64_t)canon[j] * P.ldL] = fp_add(fp_mul(cA[j], u1, P.f), fp_mul(cB[j], u0, P.f), P.f);
-            g[(int64_t)canon[j + 1] * P.ldL] = fp_mul(cA[j + 1], u0, P.f);
+            g[(int64_t)j * P.ldL] = fp_add(fp_mul(cA[j], u1, P.f), fp_mul(cB[j], u0, P.f), P.f);
+            g[(int64_t)(j + 1) * P.ldL] = fp_mul(cA[j + 1], u0, P.f);
             ++j;
         }
     }
@@ -292,48 +265,6 @@ __device__ __forceinline__ void finish_row(const PanelParams &P, const uint32_t 
 // ---------------------------------------------------------------------------
 // helper CTAs
 // ---------------------------------------------------------------------------
-
-// Post this CTA's answer to scan `sid`: the first row mn with a non-zero
-// value (INT_MAX: none).  For a hit the row's U~ values (np of them) and the
-// value x at it go to the scan's candidate slot first.  All compute threads.
-__device__ __forceinline__ void post_answer(const PanelParams &P, Shared &sh, int lo, int sid, int mn, int np,
-                                            uint32_t xval)
-{
-    const int tid = threadIdx.x;
-    if (P.test_drop == 1) return;  // failure-detection test: the answer is never sent
-    if (mn != INT_MAX) {
-        const int lr = mn - lo;
-        uint32_t *dst = P.partner_lp + ((int64_t)(sid % SCAN_RING) * MAX_PANEL_GRID + blockIdx.x) * PSTR;
-        for (int k = tid; k < np; k += NCT)
-            dst[k] = lr < SROWS ? sh.U[k * SSTRIDE + lr] : P.LpT[(int64_t)k * P.ldL + mn];
-        if (tid == 0) dst[KP_MAX] = xval;
-        __threadfence();
-        cbar();
-        if (tid == 0) {
-            atomicMin(&P.scans[sid].min, mn);
-            __threadfence();
-            atomicOr(&P.scans[sid].mask[blockIdx.x >> 5], 1u << (blockIdx.x & 31));
-            atomicAdd(&P.scans[sid].done, 1);
-        }
-    } else if (tid == 0) {
-        atomicOr(&P.scans[sid].mask[blockIdx.x >> 5], 1u << (blockIdx.x & 31));
-        atomicAdd(&P.scans[sid].done, 1);
-    }
-}
-
-// CTA-wide minimum of v over the compute threads (all of them call it).
-__device__ __forceinline__ int cta_min(Shared &sh, int v)
-{
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if (lane == 0) sh.redi[warp] = v;
-    cbar();
-    int mn = INT_MAX;
-    for (int i = 0; i < NCW; ++i) mn = min(mn, sh.redi[i]);
-    cbar();
-    return mn;
-}
-
 template <bool BIG>
 __device__ void helper_cta(const PanelParams &P, Shared &sh, int lo, int hi)
 {
@@ -380,10 +311,11 @@ __device__ void helper_cta(const PanelParams &P, Shared &sh, int lo, int hi)
                 ringv[lane + 30] = c1;
                 if (lane + 64 < NCH) ringv[lane + 62] = c2;
                 const int kind = __shfl_sync(0xffffffffu, (int)c0.x, 0);
-                if (kind == EV_END || kind == EV_FARPAIR) {
-                    // these records carry up to 4*KP_MAX payload words
-                    for (int k = 2 * KP_MAX / 4 + lane; k < EV_WORDS / 4; k += 32) ringv[k] = __ldcg(rec + 2 + k);
-                    end = end || kind == EV_END;
+                if (kind == EV_END) {
+                    // the end record carries 3*KP_MAX payload words
+                    for (int k = 2 * KP_MAX / 4 + lane; k < 3 * KP_MAX / 4; k += 32)
+                        ringv[k] = __ldcg(rec + 2 + k);
+                    end = true;
                 }
             }
             __threadfence_block();
@@ -444,6 +376,19 @@ __device__ void helper_cta(const PanelParams &P, Shared &sh, int lo, int hi)
                 // t > a for every far row t: column a of row t
                 const int c = ea & 3;
                 for (int lr = lane; lr < nr; lr += 32) sh.scol[s][0][lr] = pick4(sh.sgrp[bi][lr], c);
+                if (kind == EV_PIVOT2) {
+                    // S(t, b): for t > b one line per row, so all loads of the
+                    // lane go out before the first store (one round trip)
+                    uint32_t v[SROWS / 32];
+#pragma unroll
+                    for (int i = 0; i < SROWS / 32; ++i) {
+                        const int lr = lane + 32 * i;
+                        v[i] = lr < nr ? s_at(P.S, P.ldS, lo + lr, eb) : 0u;
+                    }
+#pragma unroll
+                    for (int i = 0; i < SROWS / 32; ++i)
+                        if (lane + 32 * i < nr) sh.scol[s][1][lane + 32 * i] = v[i];
+                }
                 __syncwarp();
                 if (gbuf_g[bi ^ 1] != g + 1) {
                     // prefetch the next group into the other buffer once nothing is in flight
@@ -452,19 +397,6 @@ __device__ void helper_cta(const PanelParams &P, Shared &sh, int lo, int hi)
                     fetch_grp(g + 1, bi ^ 1);
                     last_g = g + 1;
                 }
-            }
-            if (kind == EV_PIVOT2 || kind == EV_FARPAIR) {
-                // S(t, b): for t > b one line per row, so all loads of the lane go
-                // out before the first store (one round trip)
-                uint32_t v[SROWS / 32];
-#pragma unroll
-                for (int i = 0; i < SROWS / 32; ++i) {
-                    const int lr = lane + 32 * i;
-                    v[i] = lr < nr ? s_at(P.S, P.ldS, lo + lr, eb) : 0u;
-                }
-#pragma unroll
-                for (int i = 0; i < SROWS / 32; ++i)
-                    if (lane + 32 * i < nr) sh.scol[s][1][lane + 32 * i] = v[i];
             }
             __threadfence_block();
             __syncwarp();
@@ -476,92 +408,49 @@ __device__ void helper_cta(const PanelParams &P, Shared &sh, int lo, int hi)
     }
     // ---- compute warps ----
     const int half = tid & 1;
+    CHAIN_PROF(long long hidle = 0, hbusy = 0, hmark = clock64();)
+    auto hflush = [&]() {
+        if (tid == 0 && blockIdx.x == 1) {
+            CHAIN_PROF(P.out->dbg[5] = hidle; P.out->dbg[6] = hbusy;)
+        }
+    };
     for (int e = 0;; ++e) {
         if (tid == 0) {
+            CHAIN_PROF(const long long tw = clock64(); hbusy += tw - hmark;)
             Spin sp;
             while (sh.ev_ready <= e && !sh.quit) {
                 __nanosleep(32);
                 if (sp.expired(2 * P.budget_ns + 1000000)) break;
             }
+            CHAIN_PROF(hmark = clock64(); hidle += hmark - tw;)
+            if (blockIdx.x == 1) P.out->dbg[7] = e;
             sh.hgo = sh.ev_ready > e;  // one decision for every compute thread
         }
         cbar();
-        if (!sh.hgo) return;  // quit or abort
+        if (!sh.hgo) { hflush(); return; }  // quit or abort
         __threadfence_block();
         const int s = e % NSLOT;
         const int kind = sh.ev[s].kind;
-        const int np = sh.ev[s].np, a = sh.ev[s].a, b = sh.ev[s].b, col = sh.ev[s].col;
+        const int np = sh.ev[s].np, a = sh.ev[s].a, b = sh.ev[s].b;
         const uint32_t W = sh.ev[s].s0;
         const uint32_t *za = sh.ring[s];
         const uint32_t *zb = sh.ring[s] + KP_MAX;
         if (kind == EV_END) {
-            // rewrite this CTA's rows as true L columns in pivot order
+            // rewrite this CTA's rows as true L columns
             const uint32_t *kinds = sh.ring[s];
             const uint32_t *cA = sh.ring[s] + KP_MAX;
             const uint32_t *cB = sh.ring[s] + 2 * KP_MAX;
-            const uint32_t *canon = sh.ring[s] + 3 * KP_MAX;
+            for (int k = tid; k < np; k += NCT) sh.kind[k] = (uint8_t)kinds[k];
+            cbar();
             for (int lr = tid; lr < nrows; lr += NCT) {
                 const int t = lo + lr;
-                if (lr < SROWS) finish_row(P, sh.U + lr, SSTRIDE, t, np, kinds, cA, cB, canon);
-                else finish_row(P, P.LpT + t, (int)P.ldL, t, np, kinds, cA, cB, canon);
+                if (lr < SROWS) finish_row(P, sh.U + lr, SSTRIDE, P.LpC + t, np, sh.kind, cA, cB);
+                else finish_row(P, P.LpT + t, (int)P.ldL, P.LpC + t, np, sh.kind, cA, cB);
             }
+            hflush();
             return;
         }
-        if (kind == EV_FARPAIR) {
-            // the far pair's columns: c~_a from the scan's own column, c~_b by
-            // a pass with z_b; then the rank-1 fixes of the later columns
-            const int ncorr = sh.ev[s].aux & 0xffff, nres = sh.ev[s].aux >> 16;
-            const uint32_t *corr = sh.ring[s] + KP_MAX;
-            const uint32_t *resc = sh.ring[s] + EV_WORDS;
-            const uint32_t *scP = P.scancol + (int64_t)(sh.ev[s].scan_id % SCAN_RING) * P.ldL;
-            for (int base = 0; base < nrows; base += NCT / 2) {
-                const int lr = base + (tid >> 1);
-                const bool valid = lr < nrows;
-                const bool sm = lr < SROWS;
-                const int t = lo + lr;
-                const uint32_t sb = valid ? (sm ? sh.scol[s][1][lr] : s_at(P.S, P.ldS, t, b)) : 0u;
-                const uint32_t ubv = schur2<BIG>(P, sh.U, lr, t, sb, W, za, np, half, valid, sm);
-                if (valid && half == 0) {
-                    const uint32_t uav = scP[t];
-                    if (sm) { sh.U[col * SSTRIDE + lr] = uav; sh.U[(col + 1) * SSTRIDE + lr] = ubv; }
-                    P.LpT[(int64_t)col * P.ldL + t] = uav;
-                    P.LpT[(int64_t)(col + 1) * P.ldL + t] = ubv;
-                    for (int q = 0; q < ncorr; ++q) {
-                        const int c = (int)corr[2 * q];
-                        const uint32_t rho = corr[2 * q + 1];
-                        uint32_t *gp = P.LpT + (int64_t)c * P.ldL + t;
-                        const uint32_t old = sm ? sh.U[c * SSTRIDE + lr] : *gp;
-                        const uint32_t nv = fp_sub(old, fp_mul(uav, rho, P.f), P.f);
-                        if (sm) sh.U[c * SSTRIDE + lr] = nv;
-                        *gp = nv;
-                    }
-                }
-            }
-            cbar();
-            // the later scans, fixed and answered under their new ids
-            for (int q = 0; q < nres; ++q) {
-                const int so = (int)resc[-3 * (q + 1)], sn = (int)resc[-3 * (q + 1) + 1];
-                const uint32_t rho = resc[-3 * (q + 1) + 2];
-                const uint32_t *cold = P.scancol + (int64_t)(so % SCAN_RING) * P.ldL;
-                uint32_t *cnew = P.scancol + (int64_t)(sn % SCAN_RING) * P.ldL;
-                int firstnz = INT_MAX;
-                for (int lr = tid; lr < nrows; lr += NCT) {
-                    const int t = lo + lr;
-                    const uint32_t uav = lr < SROWS ? sh.U[col * SSTRIDE + lr] : P.LpT[(int64_t)col * P.ldL + t];
-                    const uint32_t c = fp_sub(cold[t], fp_mul(uav, rho, P.f), P.f);
-                    cnew[t] = c;
-                    if (c != 0 && t < firstnz) firstnz = t;
-                }
-                const int mn = cta_min(sh, firstnz);
-                const uint32_t xv = mn != INT_MAX ? cnew[mn] : 0u;
-                post_answer(P, sh, lo, sn, mn, col + 2, xv);
-            }
-            cbar();
-            if (tid == 0) { __threadfence_block(); sh.ev_done = e + 1; }
-            continue;
-        }
         int firstnz = INT_MAX;
-        uint32_t *cscan = (kind == EV_SCAN) ? P.scancol + (int64_t)(sh.ev[s].scan_id % SCAN_RING) * P.ldL : nullptr;
         for (int base = 0; base < nrows; base += NCT / 2) {
             const int lr = base + (tid >> 1);
             const bool valid = lr < nrows;
@@ -571,28 +460,50 @@ __device__ void helper_cta(const PanelParams &P, Shared &sh, int lo, int hi)
             if (kind == EV_PIVOT1) {
                 const uint32_t c = schur2<BIG>(P, sh.U, lr, t, sa, W, za, np, half, valid, sm);
                 if (valid && half == 0) {
-                    if (sm) sh.U[col * SSTRIDE + lr] = c;
-                    P.LpT[(int64_t)col * P.ldL + t] = c;
+                    if (sm) sh.U[np * SSTRIDE + lr] = c;
+                    P.LpT[(int64_t)np * P.ldL + t] = c;
                 }
             } else if (kind == EV_PIVOT2) {
                 const uint32_t sb = valid ? (sm ? sh.scol[s][1][lr] : s_at(P.S, P.ldS, t, b)) : 0u;
                 const uint32_t ca = schur2<BIG>(P, sh.U, lr, t, sa, W, za, np, half, valid, sm);
                 const uint32_t cb = schur2<BIG>(P, sh.U, lr, t, sb, W, zb, np, half, valid, sm);
                 if (valid && half == 0) {
-                    if (sm) { sh.U[col * SSTRIDE + lr] = ca; sh.U[(col + 1) * SSTRIDE + lr] = cb; }
-                    P.LpT[(int64_t)col * P.ldL + t] = ca;
-                    P.LpT[(int64_t)(col + 1) * P.ldL + t] = cb;
+                    if (sm) { sh.U[np * SSTRIDE + lr] = ca; sh.U[(np + 1) * SSTRIDE + lr] = cb; }
+                    P.LpT[(int64_t)np * P.ldL + t] = ca;
+                    P.LpT[(int64_t)(np + 1) * P.ldL + t] = cb;
                 }
-            } else {  // EV_SCAN: keep the column (a far pair reads it) and find its first non-zero
+            } else {  // EV_SCAN
                 const uint32_t c = schur2<BIG>(P, sh.U, lr, t, sa, W, za, np, half, valid, sm);
-                if (valid && half == 0) cscan[t] = c;
                 if (valid && c != 0 && t < firstnz) firstnz = t;
             }
         }
-        if (kind == EV_SCAN) {
-            const int mn = cta_min(sh, firstnz);
-            const uint32_t xv = mn != INT_MAX ? cscan[mn] : 0u;
-            post_answer(P, sh, lo, sh.ev[s].scan_id, mn, np, xv);
+        if (kind == EV_SCAN && P.test_drop != 1) {
+            for (int o = 16; o > 0; o >>= 1) firstnz = min(firstnz, __shfl_xor_sync(0xffffffffu, firstnz, o));
+            if (lane == 0) sh.redi[warp] = firstnz;
+            cbar();
+            int mn = INT_MAX;
+            for (int i = 0; i < NCW; ++i) mn = min(mn, sh.redi[i]);
+            const int sid = sh.ev[s].scan_id;
+            if (mn != INT_MAX) {
+                // a hit: publish the candidate's columns, then the row index, then the count
+                const int lr = mn - lo;
+                uint32_t *dst = P.partner_lp +
+                                ((int64_t)(sid % SCAN_RING) * MAX_PANEL_GRID + blockIdx.x) * PSTR;
+                for (int k = tid; k < np; k += NCT)
+                    dst[k] = lr < SROWS ? sh.U[k * SSTRIDE + lr] : P.LpT[(int64_t)k * P.ldL + mn];
+                __threadfence();
+                cbar();
+                if (tid == 0) {
+                    atomicMin(&P.scans[sid].min, mn);
+                    __threadfence();
+                    atomicOr(&P.scans[sid].mask[blockIdx.x >> 5], 1u << (blockIdx.x & 31));
+                    atomicAdd(&P.scans[sid].done, 1);
+                }
+            } else if (tid == 0) {
+                // a miss: nothing to order before the answer bit and the count
+                atomicOr(&P.scans[sid].mask[blockIdx.x >> 5], 1u << (blockIdx.x & 31));
+                atomicAdd(&P.scans[sid].done, 1);
+            }
         }
         cbar();
         if (tid == 0) { __threadfence_block(); sh.ev_done = e + 1; }
@@ -610,11 +521,13 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
     const FieldP f = P.f;
     const int w = P.w;
     const int nh = gridDim.x - 1;
-    for (int t = tid; t < W0; t += blockDim.x) sh.rinfo[t] = RI_UNDEC;
+    for (int t = tid; t < W0; t += blockDim.x) sh.wstate[t] = 0;
     for (int i = tid; i < SRING; i += blockDim.x) sh.res_ok[i] = 0;
     if (tid == 0) {
-        sh.abort = 0; sh.ev_ready = 0; sh.ev_done = 0; sh.quit = 0;
-        sh.nscan_pub = 0; sh.head_new = 0; sh.head_b = -1;
+        sh.np = 0; sh.ia = 0; sh.nzero = 0; sh.nscan = 0; sh.abort = 0; sh.nblk = 0;
+        sh.ev_ready = 0; sh.ev_done = 0; sh.quit = 0; sh.W = 1u;
+        sh.nscan_pub = 0; sh.ph_new = 0;
+        sh.rb = -1; sh.nrollback = 0;
         for (int i = 0; i < 16; ++i) sh.dbg[i] = 0;
     }
     __syncthreads();
@@ -644,12 +557,10 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
                 const int s = ee % NSLOT;
                 const int kind = sh.ev[s].kind, np = sh.ev[s].np;
                 uint32_t *rec = P.evlog + (int64_t)ee * EV_REC;
-                if (kind == EV_END || kind == EV_FARPAIR) {
-                    for (int k = lane; k < EV_WORDS; k += 32) rec[8 + k] = sh.ring[s][k];
-                } else {
-                    const int words = kind == EV_PIVOT2 ? 2 * KP_MAX : KP_MAX;
-                    for (int k = lane; k < words; k += 32)
-                        if (k % KP_MAX < np) rec[8 + k] = sh.ring[s][k];
+                const int words = (kind == EV_END) ? 3 * KP_MAX : (kind == EV_PIVOT2 ? 2 * KP_MAX : KP_MAX);
+                for (int k = lane; k < words; k += 32) {
+                    const int kk = k % KP_MAX;
+                    if (kind == EV_END || kk < np) rec[8 + k] = sh.ring[s][k];
                 }
                 if (lane < 8) rec[lane] = reinterpret_cast<const uint32_t *>(&sh.ev[s])[lane];
                 if (kind == EV_SCAN) {
@@ -660,17 +571,6 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
                         P.scans[sid].min = INT_MAX;
                     }
                     last_scan = sid;
-                } else if (kind == EV_FARPAIR) {
-                    const int nres = sh.ev[s].aux >> 16;
-                    for (int q = 0; q < nres; ++q) {
-                        const int sid = (int)sh.ring[s][EV_WORDS - 3 * (q + 1) + 1];
-                        if (lane < 8) P.scans[sid].mask[lane] = 0u;
-                        if (lane == 0) {
-                            P.scans[sid].done = 0;
-                            P.scans[sid].min = INT_MAX;
-                        }
-                        last_scan = sid > last_scan ? sid : last_scan;
-                    }
                 }
                 end = end || (kind == EV_END);
             }
@@ -678,6 +578,8 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
             __syncwarp();
             if (lane == 0) {
                 atomicExch(&P.sync->ev_count, ready);
+                sh.dbg[8] += 1;
+                sh.dbg[9] += ready - e;
                 sh.ev_done = ready;
                 if (last_scan >= 0) sh.nscan_pub = last_scan + 1;  // the watcher may poll those slots now
             }
@@ -771,7 +673,8 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
     const int half = tid & 1;
     const int lr = tid >> 1;  // window row of this thread pair
     const bool inwin = lr < w;
-    int ncol = 0, ia = 0, nscan = 0, ph = 0, pt = 0, ev_next = 0, nev = 0;
+    int np = 0, ia = 0, nzero = 0, nscan = 0, ph = 0, pt = 0, ev_next = 0, nrb = 0;
+    int force_b = -1, force_sid = -1;
     uint32_t W = 1u;
     // S[lr][4g .. 4g+3] of this thread's window row for the current column
     // group g = a / 4 and the next one: one 16-byte load per four rows, issued
@@ -793,13 +696,15 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
             }
         }
     };
-    // control warp (the last compute warp): settle the head of the FIFO.  Posts
-    // head_new = the head after the answered scans that found no partner, and
-    // head_b = the partner found by the scan there (-1: unanswered or none).
+    // the control warp (lane 0 is CTL): take in the answered scans.  Posts
+    // the new head (the first pending scan that is unanswered or found a
+    // partner) and a rollback request: the earliest answered scan that found a
+    // partner (-1 if none), even while older scans are still unanswered; they
+    // stay pending and may roll the panel back further.
     auto resolved = [&](int id) { return ld_acquire_cta(&sh.res_ok[id % SRING]) == id + 1; };
-    auto check_head = [&](bool wait) {
-        __syncwarp();
-        if (wait && ph < pt) {
+    auto check_scans = [&](bool wait_oldest) {
+        __syncwarp();  // the pend_* records written by CTL
+        if (wait_oldest && ph < pt) {
             if (lane == 0) {
                 const int id = sh.pend_id[ph % NPEND];
                 Spin sp;
@@ -813,7 +718,7 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
         }
         const int q = ph + lane;  // pt - ph <= NPEND < 32
         bool res = false, hit = false;
-        int v = -1;
+        int v = 0;
         if (q < pt) {
             const int id = sh.pend_id[q % NPEND];
             if (resolved(id)) {  // the answer is read only after its flag
@@ -822,207 +727,70 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
                 hit = v >= w && v < P.m;
             }
         }
-        const unsigned miss = __ballot_sync(0xffffffffu, res && !hit);
-        const int adv = __ffs(~miss) - 1;
-        const int vb = __shfl_sync(0xffffffffu, hit ? v : -1, adv & 31);
+        const unsigned rm = __ballot_sync(0xffffffffu, res), hm = __ballot_sync(0xffffffffu, hit);
+        const int head = __ffs(~rm | hm) - 1;
+        const int first = hm ? __ffs(hm) - 1 : -1;
+        const int vb = __shfl_sync(0xffffffffu, v, first < 0 ? 0 : first);
         if (lane == 0) {
-            sh.head_new = ph + adv;
-            sh.head_b = vb;
+            sh.ph_new = ph + head;
+            sh.rb = first < 0 ? -1 : ph + first;
+            sh.rb_b = vb;
         }
+    };
+    // all compute threads: roll back to pending scan k, which found partner b
+    auto rollback = [&](int k, int bfound) {
+        const int slot = k % NPEND;
+        const int ak = sh.pend_row[slot], npk = sh.pend_np[slot];
+        for (int j = npk + tid; j < np; j += NCT)
+            if (sh.kind[j] == K_2B) P.consumed[sh.piv_rows[j]] = 0;
+        for (int t = ak + tid; t < w; t += NCT) sh.wstate[t] = 0;
+        cbar();
+        for (int j = tid; j < npk; j += NCT) {
+            if (sh.kind[j] == K_2B) {
+                const int bb = sh.piv_rows[j];
+                if (bb >= ak && bb < w) sh.wstate[bb] = 1;
+            }
+            sh.bw[j] = sh.pend_bw[slot][j];
+        }
+        for (int q = tid; q < (np - npk) * w; q += NCT) {
+            const int j = npk + q / w, t = q % w;
+            sh.U[j * SSTRIDE + t] = 0;
+            P.LpT[(int64_t)j * P.ldL + t] = 0;
+        }
+        np = npk;
+        nzero = sh.pend_nz[slot];
+        ia = ak;
+        W = sh.pend_W[slot];
+        force_b = bfound;
+        force_sid = sh.pend_id[slot];
+        pt = k;  // this and every later pending scan are dropped; older ones stay
+        ++nrb;
+        cbar();
     };
 
-    // A far scan found its partner: insert the far pair at the head of the
-    // FIFO (all compute threads; ph is its index).
-    auto handle_hit = [&](int b) {
-        const int hs = ph % NPEND;
-        const int aP = sh.pend_row[hs], sidP = sh.pend_id[hs], evP = sh.pend_ev[hs];
-        const uint32_t Wsc = sh.pend_W[hs];
-        const int chunk = (P.m - w + nh - 1) / nh;
-        const int owner = 1 + (b - w) / chunk;
-        const uint32_t *src = P.partner_lp + ((int64_t)(sidP % SCAN_RING) * MAX_PANEL_GRID + owner) * PSTR;
-        uint32_t sbb = 0u;
-        if (tid < ncol) sh.ub[tid] = __ldcg(src + tid);
-        if (tid == 0) {
-            sh.xy[0] = __ldcg(src + KP_MAX);
-            sbb = s_at(P.S, P.ldS, b, b);
-        }
-        cbar();
-        // z_b over the columns that precede row aP; far pairs weigh W / delta
-        if (tid < ncol) {
-            const int jb = tid - (sh.kind[tid] == K_2B);
-            uint32_t zv = 0u;
-            if (sh.brow[jb] < aP) {
-                const uint32_t wt = sh.isfar[jb] ? fp_mul(Wsc, sh.invd[jb], f) : sh.pend_bw[hs][jb];
-                zv = zval_w(tid, sh.ub, 1, sh, wt, f);
-            }
-            sh.zt[tid] = zv;
-        }
-        cbar();
-        const uint32_t x = sh.xy[0];
-        if (warp == 0) {
-            // y~ = W S(b,b) - U~[b] . z_b
-            uint64_t ay = 0;
-            for (int k = lane; k < ncol; k += 32) mac<true>(ay, sh.ub[k], sh.zt[k], f);
-            uint64_t sy = fp_reduce64(ay, f);
-            for (int o = 16; o > 0; o >>= 1) sy += __shfl_xor_sync(0xffffffffu, sy, o);
-            if (lane == 0) sh.xy[1] = fp_sub(fp_mul(Wsc, sbb, f), fp_reduce64(sy, f), f);
-        }
-        // the block's window column c~_b[t] for the window rows t >= aP (t < b)
-        const bool rowb = inwin && lr >= aP;
-        const uint32_t s_b = rowb ? __ldg(P.S + (int64_t)b * P.ldS + lr) : 0u;
-        const uint32_t cb_t = schur2<BIG>(P, sh.U, lr, lr, s_b, Wsc, sh.zt, ncol, half, rowb, true);
-        if (tid == 32) sh.xy[2] = fp_inv(fp_mul(Wsc, fp_mul(x, x, f), f), f);  // 1 / delta
-        if (tid == NCT - 1) ring_ready(ev_next);
-        cbar();
-        const uint32_t y = sh.xy[1], invd = sh.xy[2];
-        const int colP = ncol;
-        if (rowb && half == 0) {
-            sh.U[colP * SSTRIDE + lr] = 0u;  // c~_a = 0 on the window rows after aP
-            sh.U[(colP + 1) * SSTRIDE + lr] = cb_t;
-            P.LpT[(int64_t)colP * P.ldL + lr] = 0u;
-            P.LpT[(int64_t)(colP + 1) * P.ldL + lr] = cb_t;
-        }
-        const int slot = ev_next % NSLOT;
-        for (int k = tid; k < ncol; k += NCT) sh.ring[slot][k] = sh.zt[k];
-        cbar();
-        if (warp == 0) {
-            // ---- the fixes of the later blocks' far columns (one warp) ----
-            // rho_i = ext_i - sum_l rho_l z_i[c_l] over the corrected columns
-            // c_l of earlier events; lanes hold the columns, each with the
-            // block weight it had at the event being processed.
-            int lcol[LPL], lkd[LPL];
-            uint32_t lbw[LPL], lrho[LPL];
-#pragma unroll
-            for (int q = 0; q < LPL; ++q) { lcol[q] = 0; lkd[q] = 0; lbw[q] = 0u; lrho[q] = 0u; }
-            int nl = 0, ncorr = 0, nres = 0;
-            const uint32_t xe = fp_mul(x, invd, f);
-            uint32_t *corr = sh.ring[slot] + KP_MAX;
-            uint32_t *resc = sh.ring[slot] + EV_WORDS;
-            auto rho_of = [&](int u, uint32_t We) -> uint32_t {
-                // ext = z_u[colP] = x~ c~_b[u] W_e / delta  (c~_a[u] = 0)
-                const uint32_t ext = fp_mul(fp_mul(xe, sh.U[(colP + 1) * SSTRIDE + u], f), We, f);
-                uint64_t acc = 0;
-#pragma unroll
-                for (int q = 0; q < LPL; ++q) {
-                    if (lane + 32 * q < nl) {
-                        const int c = lcol[q];
-                        uint32_t zc;
-                        if (lkd[q] == K_1x1) zc = sh.U[c * SSTRIDE + u];
-                        else if (lkd[q] == K_2A)
-                            zc = fp_sub(fp_mul(sh.mx[c], sh.U[(c + 1) * SSTRIDE + u], f),
-                                        fp_mul(sh.my[c], sh.U[c * SSTRIDE + u], f), f);
-                        else zc = fp_mul(sh.mx[c - 1], sh.U[(c - 1) * SSTRIDE + u], f);
-                        acc += fp_mul(lrho[q], fp_mul(zc, lbw[q], f), f);
-                    }
-                }
-                uint64_t tot = fp_reduce64(acc, f);
-                for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
-                return fp_sub(ext, fp_reduce64(tot, f), f);
-            };
-            for (int e = evP + 1; e < nev; ++e) {
-                const int es = e % EVT;
-                const int ek = sh.evt_kind[es], u = sh.evt_u[es], ecol = sh.evt_col[es];
-                const uint32_t We = sh.evt_W[es];
-                if (ek == EK_SCAN) {
-                    const uint32_t rho = rho_of(u, We);
-                    const int so = sh.evt_sid[es], sn = nscan + nres;
-                    __syncwarp();
-                    if (lane == 0) {
-                        resc[-3 * (nres + 1)] = (uint32_t)so;
-                        resc[-3 * (nres + 1) + 1] = (uint32_t)sn;
-                        resc[-3 * (nres + 1) + 2] = rho;
-                        sh.evt_sid[es] = sn;
-                        sh.pend_id[(ph + 1 + nres) % NPEND] = sn;
-                    }
-                    ++nres;
-                    continue;
-                }
-                const uint32_t r0 = rho_of(u, We);
-                const uint32_t r1 = (ek == EK_P2) ? rho_of(sh.evt_v[es], We) : 0u;
-                if (lane == 0) {
-                    corr[2 * ncorr] = (uint32_t)ecol;
-                    corr[2 * ncorr + 1] = r0;
-                    if (ek == EK_P2) {
-                        corr[2 * ncorr + 2] = (uint32_t)(ecol + 1);
-                        corr[2 * ncorr + 3] = r1;
-                    }
-                }
-                ncorr += (ek == EK_P2) ? 2 : 1;
-                // the event's block: older columns' weights grow by its delta,
-                // its own columns start at the event's scale
-                const uint32_t dl = sh.delta[ecol];
-#pragma unroll
-                for (int q = 0; q < LPL; ++q)
-                    if (lane + 32 * q < nl) lbw[q] = fp_mul(lbw[q], dl, f);
-                const int nadd = (ek == EK_P2) ? 2 : 1;
-                for (int i = 0; i < nadd; ++i) {
-                    const int l = nl + i;
-                    if ((l & 31) == lane) {
-#pragma unroll
-                        for (int q = 0; q < LPL; ++q)
-                            if (q == (l >> 5)) {
-                                lcol[q] = ecol + i;
-                                lkd[q] = (ek == EK_P1) ? K_1x1 : (i == 0 ? K_2A : K_2B);
-                                lbw[q] = We;
-                                lrho[q] = i == 0 ? r0 : r1;
-                            }
-                    }
-                }
-                nl += nadd;
-            }
-            if (lane == 0) { sh.ncorr = ncorr; sh.nres = nres; }
-        }
-        cbar();
-        const int ncorr = sh.ncorr, nres = sh.nres;
-        if (tid == 0) {
-            sh.kind[colP] = K_2A; sh.kind[colP + 1] = K_2B;
-            sh.isfar[colP] = 1; sh.isfar[colP + 1] = 1;
-            sh.bw[colP] = fp_mul(W, invd, f);  // W / delta at the current scale
-            sh.mx[colP] = x; sh.my[colP] = y; sh.piv[colP] = x; sh.w0[colP] = Wsc;
-            sh.invd[colP] = invd; sh.delta[colP] = 0u;
-            sh.brow[colP] = aP; sh.brow[colP + 1] = aP;
-            sh.piv_rows[colP] = aP; sh.piv_rows[colP + 1] = b;
-            sh.rinfo[aP] = RI_PIV + colP;
-            P.consumed[b] = 1;
-            Event &ev = sh.ev[slot];
-            ev.kind = EV_FARPAIR; ev.a = aP; ev.b = b; ev.np = ncol; ev.s0 = Wsc; ev.col = colP;
-            ev.scan_id = sidP; ev.aux = ncorr | (nres << 16);
-            __threadfence_block();
-            sh.ev_ready = ev_next + 1;
-            sh.dbg[2] += 1;
-            sh.dbg[3] += ncorr;
-            sh.dbg[4] += nres;
-        }
-        ncol += 2;
-        nscan += nres;
-        ++ph;
-        ++ev_next;
-    };
-    // settle the head: the answered misses become zero rows; a hit is inserted
-    auto settle = [&](int hn, int hb) {
-        for (int q = ph + tid; q < hn; q += NCT) sh.rinfo[sh.pend_row[q % NPEND]] = RI_ZERO;
-        ph = hn;
-        if (hb >= 0) handle_hit(hb);
-        cbar();
+    long long cyc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    CHAIN_PROF(long long tmark = clock64();)
+    auto lap = [&](int phz) {
+        CHAIN_PROF(if (tid == 0) { const long long t = clock64(); cyc[phz] += t - tmark; tmark = t; })
+        (void)phz;
     };
 
     for (;;) {
-        const int np_pend = pt - ph;
-        const bool room = ia < w && ncol + 2 * np_pend + 2 <= P.kp && ev_next < MAX_EVENTS - 64 &&
-                          nscan < MAX_SCANS - 2 * NPEND - 2 &&
-                          (np_pend == 0 || nev - sh.pend_ev[ph % NPEND] < EVT_LIM);
-        if (!room) {
+        const bool full = np > P.kp - 2 || ia >= w || ev_next > MAX_EVENTS - 64 || nscan > MAX_SCANS - 64;
+        if (full) {
             if (ph == pt) break;  // nothing in flight: the panel is complete
-            if (warp == NCW - 1) check_head(true);
+            if (warp == NCW - 1) check_scans(true);
             cbar();
-            const int hn = sh.head_new, hb = sh.head_b;
+            ph = sh.ph_new;
+            const int rb = sh.rb, rb_b = sh.rb_b;
             const bool ab = sh.abort;
             cbar();
             if (ab) break;
-            settle(hn, hb);
+            if (rb >= 0) rollback(rb, rb_b);
+            lap(6);
             continue;
         }
-        if (sh.rinfo[ia] != RI_UNDEC) {
+        if (sh.wstate[ia]) {
             ++ia;
             continue;
         }
@@ -1030,13 +798,13 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
         const int slot = ev_next % NSLOT;
         uint32_t *za = sh.ring[slot];
         uint32_t *zb = sh.ring[slot] + KP_MAX;
-        if (tid < ncol) {
+        if (tid < np) {
             ring_ready(ev_next);
             za[tid] = zval(tid, sh.U + a, SSTRIDE, sh, f);
         }
         if (warp == NCW - 1) {
             if (lane == 0) sh.dbg[0] += 1;
-            check_head(false);
+            check_scans(false);
         }
         const bool myrow = inwin && lr >= a;
         {
@@ -1049,124 +817,150 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
             }
         }
         const uint32_t s_col = myrow ? pick4(g_cur, a & 3) : 0u;
+        CHAIN_PROF(const long long tb1 = clock64();)
         cbar();
+        CHAIN_PROF(const long long ta1 = clock64();)
         {
-            const int hn = sh.head_new, hb = sh.head_b;
+            ph = sh.ph_new;
+            const int rb = sh.rb, rb_b = sh.rb_b;
             if (sh.abort) break;
-            if (hb >= 0) {
-                cbar();  // every thread has read the posted head
-                settle(hn, hb);
-                continue;  // the row is taken again
+            if (rb >= 0) {
+                cbar();  // every thread has read the posted request
+                rollback(rb, rb_b);
+                lap(5);
+                continue;
             }
-            // misses only: mark their rows, nothing this row needs changes
-            for (int q = ph + tid; q < hn; q += NCT) sh.rinfo[sh.pend_row[q % NPEND]] = RI_ZERO;
-            ph = hn;
         }
-        // Snapshot for this row's scan, should it issue one: a scan goes out
-        // only while pt - ph < npend <= NPEND, so slot pt % NPEND then holds no
-        // pending scan and always takes this row's weights.
-        if (tid < ncol && pt - ph < NPEND) sh.pend_bw[pt % NPEND][tid] = sh.bw[tid];
+        // Snapshot for a rollback to this row, kept if its scan is issued.  It
+        // is taken after the head update above, with the head the scan path
+        // tests: a scan goes out only while pt - ph < npend <= NPEND, so slot
+        // pt % NPEND then holds no pending scan's snapshot and always holds
+        // this row's.
+        if (tid < np && pt - ph < NPEND) sh.pend_bw[pt % NPEND][tid] = sh.bw[tid];
+        lap(0);
         // c~_a[t] for the window rows t >= a (t = a included) and the first
         // non-zero of row a beyond a inside the window, in one pass
-        const uint32_t ca_t = schur2<BIG>(P, sh.U, lr, lr, s_col, W, za, ncol, half, myrow, true);
+        const uint32_t ca_t = schur2<BIG>(P, sh.U, lr, lr, s_col, W, za, np, half, myrow, true);
         if (lr == a && half == 0) sh.caa = ca_t;
         int firstnz = (half == 0 && inwin && lr > a && ca_t != 0) ? lr : INT_MAX;
         for (int o = 16; o > 0; o >>= 1) firstnz = min(firstnz, __shfl_xor_sync(0xffffffffu, firstnz, o));
         if (lane == 0) sh.redi[warp] = firstnz;
+        CHAIN_PROF(const long long tb2 = clock64();)
         cbar();
+        CHAIN_PROF(const long long ta2 = clock64();)
+        CHAIN_PROF(if (tid == 0 || tid == NCT - 1) {
+            const int o = (tid == 0) ? 10 : 12;
+            sh.dbg[o] += ta1 - tb1;       // wait at barrier 1
+            sh.dbg[o + 1] += ta2 - tb2;   // wait at barrier 2
+            if (tid == 0) sh.dbg[14] += tb2 - ta1;  // schur phase (thread 0)
+            else sh.dbg[15] += tb2 - ta1;
+        })
+        lap(1);
         const uint32_t caa = sh.caa;
 
         if (caa != 0) {
-            // ---- 1x1 pivot: U~[:, ncol] = c~_a, delta = W c~_a[a] ----
+            // ---- 1x1 pivot: U~[:, np] = c~_a, delta = W c~_a[a] ----
             if (myrow && half == 0) {
-                sh.U[ncol * SSTRIDE + lr] = ca_t;
-                P.LpT[(int64_t)ncol * P.ldL + lr] = ca_t;
+                sh.U[np * SSTRIDE + lr] = ca_t;
+                P.LpT[(int64_t)np * P.ldL + lr] = ca_t;
             }
             const uint32_t delta = fp_mul(W, caa, f);
-            if (tid < ncol && sh.kind[tid] != K_2B) sh.bw[tid] = fp_mul(sh.bw[tid], delta, f);
+            if (tid < np && sh.kind[tid] != K_2B) sh.bw[tid] = fp_mul(sh.bw[tid], delta, f);
             if (tid == 0) {
                 if (helpers) {
                     Event &ev = sh.ev[slot];
-                    ev.kind = EV_PIVOT1; ev.a = a; ev.b = -1; ev.np = ncol; ev.s0 = W; ev.col = ncol;
+                    ev.kind = EV_PIVOT1; ev.a = a; ev.b = -1; ev.np = np; ev.s0 = W; ev.col = np;
                     ev.scan_id = 0; ev.aux = 0;
                     __threadfence_block();
                     sh.ev_ready = ev_next + 1;
                 }
-                sh.kind[ncol] = K_1x1; sh.isfar[ncol] = 0; sh.bw[ncol] = W; sh.piv[ncol] = caa; sh.w0[ncol] = W;
-                sh.delta[ncol] = delta; sh.brow[ncol] = a;
-                sh.piv_rows[ncol] = a;
-                sh.rinfo[a] = RI_PIV + ncol;
-                const int es = nev % EVT;
-                sh.evt_kind[es] = EK_P1; sh.evt_u[es] = a; sh.evt_v[es] = -1; sh.evt_col[es] = ncol;
-                sh.evt_sid[es] = -1; sh.evt_W[es] = W;
+                sh.kind[np] = K_1x1; sh.bw[np] = W; sh.piv[np] = caa; sh.w0[np] = W; sh.delta[np] = delta;
+                sh.piv_rows[np] = a;
+                sh.wstate[a] = 1;
             }
             W = fp_mul(W, delta, f);
-            ++ncol;
+            ++np;
             ++ia;
-            ++nev;
             if (helpers) ++ev_next;
             cbar();
+            lap(2);
             continue;
         }
 
         int b = INT_MAX;
-        for (int i = 0; i < NCW; ++i) b = min(b, sh.redi[i]);
+        bool far = false;
+        if (force_b >= 0) {
+            // partner found by this row's scan before the rollback
+            b = force_b;
+            far = true;
+            const int chunk = (P.m - w + nh - 1) / nh;
+            const int owner = 1 + (b - w) / chunk;
+            const uint32_t *src = P.partner_lp +
+                                  ((int64_t)(force_sid % SCAN_RING) * MAX_PANEL_GRID + owner) * PSTR;
+            if (tid < np) sh.ub[tid] = __ldcg(src + tid);
+        } else {
+            for (int i = 0; i < NCW; ++i) b = min(b, sh.redi[i]);
+        }
         if (b == INT_MAX && helpers) {
-            // ---- far scan: publish it and go on as if the row were zero ----
+            // ---- speculative far scan: publish it and go on as if the row were zero ----
             if (pt - ph >= P.npend) {
-                if (warp == NCW - 1) check_head(true);
+                if (warp == NCW - 1) check_scans(true);
                 cbar();
-                const int hn = sh.head_new, hb = sh.head_b;
+                ph = sh.ph_new;
+                const int rb = sh.rb, rb_b = sh.rb_b;
                 const bool ab = sh.abort;
                 cbar();
                 if (ab) break;
-                settle(hn, hb);
+                if (rb >= 0) rollback(rb, rb_b);
+                lap(6);
                 continue;  // the row is taken again from the top
             }
-            if (tid == NCT - 1) {
+            if (tid == CTL) {
                 Event &ev = sh.ev[slot];
-                ev.kind = EV_SCAN; ev.a = a; ev.b = -1; ev.np = ncol; ev.s0 = W; ev.col = -1;
+                ev.kind = EV_SCAN; ev.a = a; ev.b = -1; ev.np = np; ev.s0 = W; ev.col = -1;
                 ev.scan_id = nscan; ev.aux = 0;
                 const int ps = pt % NPEND;
-                sh.pend_id[ps] = nscan; sh.pend_row[ps] = a; sh.pend_ev[ps] = nev; sh.pend_W[ps] = W;
-                sh.rinfo[a] = RI_PEND;
-                const int es = nev % EVT;
-                sh.evt_kind[es] = EK_SCAN; sh.evt_u[es] = a; sh.evt_v[es] = -1; sh.evt_col[es] = -1;
-                sh.evt_sid[es] = nscan; sh.evt_W[es] = W;
-                sh.dbg[5] += 1;
+                sh.pend_id[ps] = nscan; sh.pend_row[ps] = a; sh.pend_np[ps] = np;
+                sh.pend_nz[ps] = nzero; sh.pend_W[ps] = W;
+                sh.zero_rows[nzero] = a; sh.zero_np[nzero] = np;
+                sh.wstate[a] = 1;
                 __threadfence_block();
                 sh.ev_ready = ev_next + 1;
             }
             ++nscan;
             ++pt;
+            ++nzero;
             ++ia;
             ++ev_next;
-            ++nev;
-            cbar();
+            lap(3);
             continue;
         }
         if (b == INT_MAX) {
             // ---- zero row (no far rows to search) ----
-            if (tid == 0) sh.rinfo[a] = RI_ZERO;
+            if (tid == 0) {
+                sh.zero_rows[nzero] = a; sh.zero_np[nzero] = np;
+                sh.wstate[a] = 1;
+            }
+            ++nzero;
             ++ia;
-            cbar();
             continue;
         }
 
-        // ---- 2x2 pivot on (a, b), both in the window ----
+        // ---- 2x2 pivot on (a, b) ----
+        // S(a, b) and S(b, b) for x~ and y~, loaded before the z work below
         uint32_t s_ab = 0u, s_bb = 0u;
         if (tid == 0) {
             s_ab = s_at(P.S, P.ldS, a, b);
             s_bb = s_at(P.S, P.ldS, b, b);
         }
-        if (tid < ncol) sh.ub[tid] = sh.U[tid * SSTRIDE + b];
+        if (!far && tid < np) sh.ub[tid] = sh.U[tid * SSTRIDE + b];
         cbar();
-        if (tid < ncol) zb[tid] = zval(tid, sh.ub, 1, sh, f);
+        if (tid < np) zb[tid] = zval(tid, sh.ub, 1, sh, f);
         cbar();
         // x~ = W S(a,b) - U~[b] . z_a ;  y~ = W S(b,b) - U~[b] . z_b   (warp 0)
         if (warp == 0) {
             uint64_t ax = 0, ay = 0;
-            for (int k = lane; k < ncol; k += 32) {
+            for (int k = lane; k < np; k += 32) {
                 mac<true>(ax, sh.ub[k], za[k], f);
                 mac<true>(ay, sh.ub[k], zb[k], f);
             }
@@ -1182,57 +976,58 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
         }
         // c~_b[t] for the window rows t >= a (overlaps warp 0's work)
         const uint32_t s_b = myrow ? s_at(P.S, P.ldS, lr, b) : 0u;
-        const uint32_t cb_t = schur2<BIG>(P, sh.U, lr, lr, s_b, W, zb, ncol, half, myrow, true);
+        const uint32_t cb_t = schur2<BIG>(P, sh.U, lr, lr, s_b, W, zb, np, half, myrow, true);
         cbar();
         const uint32_t x = sh.xy[0], y = sh.xy[1];
         if (myrow && half == 0) {
-            sh.U[ncol * SSTRIDE + lr] = ca_t;  // c~_a[a] = 0 here
-            sh.U[(ncol + 1) * SSTRIDE + lr] = cb_t;
-            P.LpT[(int64_t)ncol * P.ldL + lr] = ca_t;
-            P.LpT[(int64_t)(ncol + 1) * P.ldL + lr] = cb_t;
+            sh.U[np * SSTRIDE + lr] = ca_t;  // c~_a[a] = 0 here
+            sh.U[(np + 1) * SSTRIDE + lr] = cb_t;
+            P.LpT[(int64_t)np * P.ldL + lr] = ca_t;
+            P.LpT[(int64_t)(np + 1) * P.ldL + lr] = cb_t;
         }
         const uint32_t delta = fp_mul(W, fp_mul(x, x, f), f);
-        if (tid < ncol && sh.kind[tid] != K_2B) sh.bw[tid] = fp_mul(sh.bw[tid], delta, f);
+        if (tid < np && sh.kind[tid] != K_2B) sh.bw[tid] = fp_mul(sh.bw[tid], delta, f);
         if (tid == 0) {
             if (helpers) {
                 Event &ev = sh.ev[slot];
-                ev.kind = EV_PIVOT2; ev.a = a; ev.b = b; ev.np = ncol; ev.s0 = W; ev.col = ncol;
+                ev.kind = EV_PIVOT2; ev.a = a; ev.b = b; ev.np = np; ev.s0 = W; ev.col = np;
                 ev.scan_id = 0; ev.aux = 0;
                 __threadfence_block();
                 sh.ev_ready = ev_next + 1;
             }
-            sh.kind[ncol] = K_2A; sh.kind[ncol + 1] = K_2B; sh.isfar[ncol] = 0; sh.isfar[ncol + 1] = 0;
-            sh.bw[ncol] = W; sh.mx[ncol] = x; sh.my[ncol] = y; sh.piv[ncol] = x; sh.w0[ncol] = W;
-            sh.delta[ncol] = delta; sh.brow[ncol] = a; sh.brow[ncol + 1] = a;
-            sh.piv_rows[ncol] = a; sh.piv_rows[ncol + 1] = b;
-            sh.rinfo[a] = RI_PIV + ncol;
-            sh.rinfo[b] = RI_PART;
+            sh.kind[np] = K_2A; sh.kind[np + 1] = K_2B;
+            sh.bw[np] = W; sh.mx[np] = x; sh.my[np] = y; sh.piv[np] = x; sh.w0[np] = W;
+            sh.delta[np] = delta;
+            sh.piv_rows[np] = a; sh.piv_rows[np + 1] = b;
+            sh.wstate[a] = 1;
+            if (b < w) sh.wstate[b] = 1;
             P.consumed[b] = 1;
-            const int es = nev % EVT;
-            sh.evt_kind[es] = EK_P2; sh.evt_u[es] = a; sh.evt_v[es] = b; sh.evt_col[es] = ncol;
-            sh.evt_sid[es] = -1; sh.evt_W[es] = W;
         }
         W = fp_mul(W, delta, f);
-        ncol += 2;
+        np += 2;
         ++ia;
-        ++nev;
         if (helpers) ++ev_next;
+        force_b = -1;
+        force_sid = -1;
         cbar();
+        lap(4);
     }
-    const int iend = ia;
+    if (tid == 0) {
+        sh.np = np; sh.ia = ia; sh.nzero = nzero; sh.nscan = nscan; sh.nrollback = nrb;
+    }
     cbar();
 
     // ---- end of panel: batch inversion, true D and the L coefficients ----
-    const bool aborted = sh.abort != 0;
-    if (!aborted) {
+    const int iend = ia;
+    if (!sh.abort) {
         if (tid == 0) {
-            // per block: its pivot value and its scale, inverted together (Montgomery's trick)
+            // per block: its pivot value and its W, inverted together (Montgomery's trick)
             int nv = 0;
-            for (int j = 0; j < ncol; ++j)
+            for (int j = 0; j < np; ++j)
                 if (sh.kind[j] != K_2B) { sh.bi[nv++] = sh.piv[j]; sh.bi[nv++] = sh.w0[j]; }
             uint32_t run = 1;
             for (int i = 0; i < nv; ++i) { run = fp_mul(run, sh.bi[i], f); sh.bpre[i] = run; }
-            uint32_t inv = nv ? fp_inv(run, f) : 1u;
+            uint32_t inv = nv ? fp_inv_bin(run, f) : 1u;
             for (int i = nv - 1; i >= 0; --i) {
                 const uint32_t before = i ? sh.bpre[i - 1] : 1u;
                 const uint32_t vi = sh.bi[i];
@@ -1240,7 +1035,7 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
                 inv = fp_mul(inv, vi, f);
             }
             int v = 0;
-            for (int j = 0; j < ncol; ++j) {
+            for (int j = 0; j < np; ++j) {
                 const uint8_t kd = sh.kind[j];
                 if (kd == K_1x1) {
                     const uint32_t ipiv = sh.bi[v], iw0 = sh.bi[v + 1];
@@ -1266,82 +1061,54 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
                 }
             }
         }
-        // pivot order: the blocks by their first window row, the zero rows
-        // ascending (block-wide prefix sums over the window rows)
-        {
-            const int t = tid;  // one thread per window row (NCT >= W0)
-            const int ri = (t < iend && t < W0) ? sh.rinfo[t] : RI_UNDEC;
-            const int cnt = ri >= RI_PIV ? (sh.kind[ri - RI_PIV] == K_1x1 ? 1 : 2) : 0;
-            const int zf = ri == RI_ZERO ? 1 : 0;
-            int ic = cnt, iz = zf;
-            for (int o = 1; o < 32; o <<= 1) {
-                const int vc = __shfl_up_sync(0xffffffffu, ic, o), vz = __shfl_up_sync(0xffffffffu, iz, o);
-                if (lane >= o) { ic += vc; iz += vz; }
-            }
-            if (lane == 31) { sh.redi[warp] = ic; sh.redj[warp] = iz; }
-            cbar();
-            int oc = 0, oz = 0;
-            for (int i = 0; i < warp; ++i) { oc += sh.redi[i]; oz += sh.redj[i]; }
-            const int pos = oc + ic - cnt, zpos = oz + iz - zf;
-            if (cnt) {
-                const int col = ri - RI_PIV;
-                sh.canon[col] = pos;
-                if (cnt == 2) sh.canon[col + 1] = pos + 1;
-            }
-            if (zf) {
-                P.out->zero_rows[zpos] = t;
-                P.out->zero_np[zpos] = pos;
-            }
-            if (tid == NCT - 1) sh.xy[3] = (uint32_t)(oz + iz);  // zero rows
-        }
         cbar();
-        for (int j = tid; j < ncol; j += NCT) {
-            const int k = sh.canon[j];
-            P.out->piv_rows[k] = sh.piv_rows[j];
-            P.out->dval[k] = sh.dtrue[j];
-            P.out->eval[k] = sh.etrue[j];
-        }
         if (helpers) {
-            // the end event carries the column kinds, the true-L coefficients and the order
+            for (int k = tid; k < np; k += NCT) sh.bpre[k] = sh.kind[k];
+            cbar();
+            // the end event carries the column kinds and the true-L coefficients
             const int slot = ev_next % NSLOT;
-            if (tid < ncol) {
+            if (tid < np) {
                 ring_ready(ev_next);
-                sh.ring[slot][tid] = sh.kind[tid];
+                sh.ring[slot][tid] = sh.bpre[tid];
                 sh.ring[slot][KP_MAX + tid] = sh.cA[tid];
                 sh.ring[slot][2 * KP_MAX + tid] = sh.cB[tid];
-                sh.ring[slot][3 * KP_MAX + tid] = (uint32_t)sh.canon[tid];
             }
             if (tid == 0) ring_ready(ev_next);
             cbar();
             if (tid == 0) {
                 Event &ev = sh.ev[slot];
-                ev.kind = EV_END; ev.a = -1; ev.b = -1; ev.np = ncol; ev.s0 = 0; ev.col = -1;
+                ev.kind = EV_END; ev.a = -1; ev.b = -1; ev.np = np; ev.s0 = 0; ev.col = np;
                 ev.scan_id = 0; ev.aux = 0;
                 __threadfence_block();
                 sh.ev_ready = ev_next + 1;
             }
         }
-        // rewrite the window rows as true L columns in pivot order
-        for (int k = tid; k < ncol; k += NCT) {
-            sh.bi[k] = sh.kind[k];
-            sh.bpre[k] = (uint32_t)sh.canon[k];
-        }
-        cbar();
-        for (int t = tid; t < w; t += NCT)
-            finish_row(P, sh.U + t, SSTRIDE, t, ncol, sh.bi, sh.cA, sh.cB, sh.bpre);
+        // rewrite the window rows as true L columns
+        for (int t = tid; t < w; t += NCT) finish_row(P, sh.U + t, SSTRIDE, P.LpC + t, np, sh.kind, sh.cA, sh.cB);
     }
     cbar();
     if (tid == 0) { __threadfence_block(); sh.quit = 1; }
     __threadfence();
     cbar();
 
+    // ---- report ----
+    for (int k = tid; k < np; k += NCT) {
+        P.out->piv_rows[k] = sh.piv_rows[k];
+        P.out->dval[k] = sh.dtrue[k];
+        P.out->eval[k] = sh.etrue[k];
+    }
+    for (int q = tid; q < nzero; q += NCT) {
+        P.out->zero_rows[q] = sh.zero_rows[q];
+        P.out->zero_np[q] = sh.zero_np[q];
+    }
+
     // ---- compaction of the remaining rows [iend, m) minus consumed partners ----
     const int m = P.m;
     const int len = m - iend;
     const int per = (len + NCT - 1) / NCT;
-    const int clo = iend + tid * per, chi = min(m, clo + per);
+    const int lo = iend + tid * per, hi = min(m, lo + per);
     int cnt = 0;
-    for (int t = clo; t < chi; ++t) cnt += P.consumed[t] ? 0 : 1;
+    for (int t = lo; t < hi; ++t) cnt += P.consumed[t] ? 0 : 1;
     int incl = cnt;
     for (int o = 1; o < 32; o <<= 1) {
         const int vv = __shfl_up_sync(0xffffffffu, incl, o);
@@ -1355,7 +1122,7 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
         total += sh.redi[i];
     }
     int pos = woff + incl - cnt;
-    for (int t = clo; t < chi; ++t) {
+    for (int t = lo; t < hi; ++t) {
         if (!P.consumed[t]) {
             P.sigma[pos] = t;
             P.idx_next[pos] = P.idx[t];
@@ -1363,14 +1130,17 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
         }
     }
     if (tid == 0) {
-        P.out->np = aborted ? 0 : ncol;
-        P.out->nzero = aborted ? 0 : (int)sh.xy[3];
+        P.out->np = np;
+        P.out->nzero = nzero;
         P.out->iend = iend;
         P.out->m_next = total;
-        P.out->abort = (aborted ? 1 : 0) | *((volatile int *)&P.sync->abort);
-        P.out->nscan = nscan;
-        for (int i = 0; i < 8; ++i) P.out->cyc[i] = 0;
-        for (int i = 0; i < 16; ++i) P.out->dbg[i] = sh.dbg[i];
+        P.out->abort = sh.abort | *((volatile int *)&P.sync->abort);
+        P.out->nscan = sh.nscan;
+        P.out->pad[0] = sh.nrollback;
+        for (int i = 0; i < 8; ++i) P.out->cyc[i] = cyc[i];
+        sh.dbg[4] = sh.nrollback;
+        for (int i = 0; i < 16; ++i)
+            if (i < 5 || i > 7) P.out->dbg[i] = sh.dbg[i];
     }
 }
 
