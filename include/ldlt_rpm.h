@@ -369,11 +369,16 @@ int ldlt_rpm_test_drop(int which);
 /*
  * ldlt_rpm_set_speculation -- how many far scans the pivot chain may have in
  * flight while it continues past rows whose window part is zero (1..16,
- * default 16).  A scan that finds a partner rolls the panel back to its row,
- * so the depth trades waiting against discarded work; results do not depend
+ * default LDLT_SPECULATION_DEFAULT).  A scan that finds a partner rolls the
+ * panel back to its row, so the depth trades waiting against discarded work,
+ * and every speculative row is also work for the helper CTAs that answer the
+ * scans: deeper speculation slows the answers.  Measured on GB300 (n = 16384
+ * planted, p = 2^26 - 5): 83 ms at depth 3, 77.8 at 5, 81.9 at 16; n = 32768
+ * with only 2x2 pivots, p = 2^31 - 1: 348, 337, 483 ms.  Results do not depend
  * on it.  No counterpart in the paper (a scheduling parameter of this GPU
  * organisation).  Returns LDLT_OK or LDLT_ERR_ARG.
  */
+#define LDLT_SPECULATION_DEFAULT 5
 int ldlt_rpm_set_speculation(int depth);
 
 /*

@@ -44,6 +44,7 @@ from .binding import (  # noqa: F401
     LDLT_ERR_INCONSISTENT,
     set_wait_budget_ns,
     set_speculation,
+    SPECULATION_DEFAULT,
     test_drop,
     TEST_DROP_SCAN_ANSWERS,
     TEST_DROP_UPDATE_COPIES,

@@ -40,6 +40,7 @@ EXPORTS = ["ldlt_rpm_workspace_bytes", "ldlt_rpm_factor", "rpm_from_factor", "ld
 TEST_DROP_SCAN_ANSWERS = 1   # LDLT_TEST_DROP_SCAN_ANSWERS
 TEST_DROP_UPDATE_COPIES = 2  # LDLT_TEST_DROP_UPDATE_COPIES
 BATCH_MAX_N = 512  # LDLT_BATCH_MAX_N
+SPECULATION_DEFAULT = 5  # LDLT_SPECULATION_DEFAULT
 
 
 class LdltError(RuntimeError):

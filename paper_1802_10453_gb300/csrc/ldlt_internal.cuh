@@ -99,7 +99,7 @@ struct PanelParams {
     uint32_t *zlog;         // [ZLOG_EV][2][KP_MAX]: z vectors of the leader's recent row events
     int64_t budget_ns;
     int32_t *status;
-    int npend;              // far scans allowed in flight (1..24)
+    int npend;              // far scans allowed in flight (1..16)
     int test_drop;          // LDLT_TEST_DROP_SCAN_ANSWERS: helpers never answer a far scan
 };
 

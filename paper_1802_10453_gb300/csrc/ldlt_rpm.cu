@@ -21,7 +21,7 @@
 namespace {
 
 int64_t g_budget_ns = 2000000000LL;
-int g_npend = 16;  // speculative far scans in flight (tunable)
+int g_npend = LDLT_SPECULATION_DEFAULT;  // far scans in flight
 int g_test_drop = 0;  // failure-detection tests: LDLT_TEST_DROP_*
 
 // ---- profiling (optional) --------------------------------------------------

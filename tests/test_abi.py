@@ -78,6 +78,14 @@ def test_test_drop_codes(libs):
     assert L.ldlt_rpm_test_drop(0) == 0
 
 
+def test_speculation_default_matches_header(libs):
+    hdr = open(os.path.join(ROOT, "include", "ldlt_rpm.h")).read()
+    assert int(re.search(r"#define LDLT_SPECULATION_DEFAULT\s+(\d+)", hdr).group(1)) == libs.SPECULATION_DEFAULT
+    L = libs.lib()
+    assert L.ldlt_rpm_set_speculation(0) == -1 and L.ldlt_rpm_set_speculation(17) == -1
+    assert L.ldlt_rpm_set_speculation(libs.SPECULATION_DEFAULT) == 0
+
+
 def test_effective_ops_formula(libs):
     # Section 6: r^3/3 + n^2 r - r^2 n; r = n gives n^3/3
     assert libs.effective_ops(300, 300) == pytest.approx(300 ** 3 / 3)

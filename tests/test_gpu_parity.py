@@ -279,7 +279,7 @@ def test_planted_n28000_full_scan_fifo():
     _check_planted_full_size(28000, 14000, False, 65521, 91 + 28000, lr.PATH_TC)
 
 
-@pytest.mark.parametrize("depth", [1, 2, 5, 16])
+@pytest.mark.parametrize("depth", [1, 2, 5, 9, 16])
 def test_planted_speculation_depths(depth):
     """Every speculation depth gives the same exact result.  Small depths keep
     the FIFO of speculative scans full, so rows wait for the oldest scan, are
@@ -289,7 +289,7 @@ def test_planted_speculation_depths(depth):
     try:
         _check_planted_full_size(12000, 6000, False, 65521, 17 + depth, lr.PATH_TC)
     finally:
-        lr.set_speculation(16)
+        lr.set_speculation(lr.SPECULATION_DEFAULT)
 
 
 @pytest.mark.parametrize("n,r,pairs,p", [(1, 1, 0, 65521), (7, 5, 2, 2), (100, 60, 15, 8388593),
@@ -330,7 +330,7 @@ def test_all_pairs_n3000_p2_31_elementwise(depth):
     try:
         got = gpu_factor(A, p, lr.PATH_TC)
     finally:
-        lr.set_speculation(16)
+        lr.set_speculation(lr.SPECULATION_DEFAULT)
     assert got["rank"] == ref["rank"] == r
     assert np.array_equal(got["perm"], ref["perm"].astype(np.int64))
     assert np.array_equal(got["d"], ref["d"].astype(np.int64))
