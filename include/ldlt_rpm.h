@@ -43,6 +43,8 @@ extern "C" {
 #define LDLT_ERR_NO_DEVICE  -7  /* no sm_103 device visible                         */
 #define LDLT_ERR_TOO_LARGE  -8  /* n above LDLT_NOALLOC_MAX_N (no-allocation entry) */
 #define LDLT_ERR_INCONSISTENT -9 /* device only (ldlt_rpm_solve): B not in A's column space */
+#define LDLT_ERR_INTERNAL  -10  /* device only: a panel retired no row (not expected; the
+                                     factorisation stops instead of looping) */
 
 /* ---- arithmetic paths for the level-3 updates (SYRDK, Algorithm 2) ------ */
 /* FP64 form: residues carried in doubles, products accumulated with one
@@ -87,10 +89,17 @@ int ldlt_rpm_workspace_bytes(int64_t n, uint32_t p, int path, size_t *bytes);
  *            256-byte aligned; owned by the caller, not retained after return.
  *   stream   cudaStream_t as void*.
  *
- * The call enqueues work on `stream` and returns after the last kernel has
- * been enqueued.  It reads back a few words per panel on that stream to size
- * the next launches, so it synchronises `stream` internally; results are
- * ready when the stream is.
+ * The call only enqueues work on `stream`: nothing is read back and the host
+ * does not wait; results (A, perm, e, rank, status) are ready when the stream
+ * is.  The panel loop runs on the device as one CUDA graph (a while node
+ * whose condition the last kernel of each iteration sets); the graph is built
+ * and instantiated on the first call with a given set of arguments (n, p,
+ * path, lda, every pointer, the wait budget, the speculation depth) and
+ * launched again, unchanged, by later calls with the same set (the library
+ * keeps the four most recently used).  A kept graph refers to the caller's
+ * buffers only by address.  With profiling on (ldlt_rpm_profile_enable) the
+ * same kernels run from a host loop that synchronises `stream` once per
+ * panel to time the phases.
  */
 int ldlt_rpm_factor(int64_t n, uint32_t p, uint32_t *A, int64_t lda,
                     int32_t *perm, uint32_t *e, int64_t *rank, int32_t *status,
@@ -316,8 +325,10 @@ int ldlt_rpm_batched_set_schedule(int kb, int n_cut, int kb_small);
  * call on a device, not when the library is opened.  Make that first call
  * before any stream capture begins.  A failed lookup returns LDLT_ERR_CUDA
  * and leaves an error the caller had pending untouched.  Like
- * ldlt_rpm_factor, the call reads a few words back per panel and so
- * synchronises `stream`.
+ * ldlt_rpm_factor, the call only enqueues work, as one CUDA graph: the first
+ * call with a given set of arguments builds and instantiates it (the driver
+ * keeps what an instantiated graph needs, as it does for a loaded module),
+ * and later calls with the same set launch it again and create nothing.
  *
  * Every call on a device uses the same array.  The factorisation clears, on
  * the stream, every part of its scratch that must start at zero, so one call

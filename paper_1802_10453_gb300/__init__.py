@@ -42,6 +42,7 @@ from .binding import (  # noqa: F401
     solve,
     trss,
     LDLT_ERR_INCONSISTENT,
+    LDLT_ERR_INTERNAL,
     set_wait_budget_ns,
     set_speculation,
     SPECULATION_DEFAULT,

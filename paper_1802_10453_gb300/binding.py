@@ -25,9 +25,11 @@ LDLT_ERR_TIMEOUT = -6
 LDLT_ERR_NO_DEVICE = -7
 LDLT_ERR_TOO_LARGE = -8
 LDLT_ERR_INCONSISTENT = -9
+LDLT_ERR_INTERNAL = -10
 _NAMES = {0: "LDLT_OK", -1: "LDLT_ERR_ARG", -2: "LDLT_ERR_NOT_PRIME", -3: "LDLT_ERR_P_RANGE",
           -4: "LDLT_ERR_WORKSPACE", -5: "LDLT_ERR_CUDA", -6: "LDLT_ERR_TIMEOUT",
-          -7: "LDLT_ERR_NO_DEVICE", -8: "LDLT_ERR_TOO_LARGE", -9: "LDLT_ERR_INCONSISTENT"}
+          -7: "LDLT_ERR_NO_DEVICE", -8: "LDLT_ERR_TOO_LARGE", -9: "LDLT_ERR_INCONSISTENT",
+          -10: "LDLT_ERR_INTERNAL"}
 # largest order and scratch size of ldlt_rpm_factor_noalloc (LDLT_NOALLOC_* in the header)
 NOALLOC_MAX_N = 1024
 NOALLOC_BYTES = 48 << 20
@@ -270,9 +272,10 @@ def factor_noalloc(A, p: int, perm, e, rank, status, path: int = PATH_TC, stream
 
     The caller supplies the outputs (perm, e: int32[n]; rank: int64[1];
     status: int32[1], all on A's device); this wrapper only passes pointers and
-    allocates nothing (the library call, like factor(), reads a few words back
-    per panel and so synchronises the stream).  Calls on one device share the
-    scratch array, so calls that overlap in time race; the first call on a
+    allocates nothing (the library call, like factor(), only enqueues: its
+    first call with a given set of arguments instantiates the CUDA graph of
+    the panel loop, later ones launch it again).  Calls on one device share
+    the scratch array, so calls that overlap in time race; the first call on a
     device loads the module that holds the array and should come before any
     stream capture.
     Returns dict(perm, e, rank, status, n, p); read status after the stream.

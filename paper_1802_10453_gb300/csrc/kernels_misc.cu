@@ -1,7 +1,8 @@
 // kernels_misc.cu -- the HBM-streaming steps around the pivot chain:
-// ingest of A, storing the panel's L columns, compaction of the Schur
-// complement when a panel took no pivot, the final symmetric permutation of L
+// ingest of A, storing the panel's L columns, the panel loop's state, the
+// final symmetric permutation of L
 // (PERM of Algorithm 2) and the rank profile matrix P Psi P^T (Section 2.1).
+#include "../../include/ldlt_rpm.h"
 #include "ldlt_internal.cuh"
 
 namespace {
@@ -62,54 +63,27 @@ __global__ void ingest_perm_kernel(const uint32_t *__restrict__ A, int64_t lda, 
     }
 }
 
-// Lw[idx[t]][col0 + j] = LpT[j][t]: transpose through shared memory so both
-// the reads (along t) and the writes (along j) are coalesced.
-__global__ void lw_scatter_kernel(const uint32_t *__restrict__ LpT, int64_t ldL, int m, int np,
-                                  const int *__restrict__ idx, uint32_t *__restrict__ Lw,
-                                  int64_t ldw, int col0)
+// Lw[idx[t]][r0 + j] = LpC[j][t] for the panel's np columns and m rows:
+// transpose through shared memory so both the reads (along t) and the writes
+// (along j) are coalesced.
+__global__ void lw_scatter_kernel(const uint32_t *__restrict__ LpC, int64_t ldL,
+                                  const LoopState *__restrict__ ls, const PanelOut *__restrict__ out,
+                                  const int *__restrict__ idx, uint32_t *__restrict__ Lw, int64_t ldw)
 {
+    if (!step_live(ls, out)) return;
+    const int m = ls->m, np = out->np, col0 = ls->r0;
     __shared__ uint32_t tile[32][33];
     const int t0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+    if (t0 >= m || j0 >= np) return;
     const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
     for (int r = ty; r < 32; r += 8) {
         int j = j0 + r, t = t0 + tx;
-        if (j < np && t < m) tile[r][tx] = LpT[(int64_t)j * ldL + t];
+        if (j < np && t < m) tile[r][tx] = LpC[(int64_t)j * ldL + t];
     }
     __syncthreads();
     for (int r = ty; r < 32; r += 8) {
         int t = t0 + r, j = j0 + tx;
         if (t < m && j < np) Lw[(int64_t)idx[t] * ldw + col0 + j] = tile[tx][r];
-    }
-}
-
-// Snext[i][j] = S[sigma[i]][sigma[j]] for j <= i < m_next.
-__global__ void compact_copy_kernel(const uint32_t *__restrict__ S, int64_t ldS,
-                                    const int *__restrict__ sigma, int m_next,
-                                    uint32_t *__restrict__ Snext)
-{
-    const int i = blockIdx.y;
-    if (i >= m_next) return;
-    const uint32_t *src = S + (int64_t)sigma[i] * ldS;
-    uint32_t *dst = Snext + (int64_t)i * ldS;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j <= i; j += gridDim.x * blockDim.x)
-        dst[j] = src[sigma[j]];
-}
-
-// Append the panel's pivots, D and zero rows (as original indices) to the
-// global lists.
-__global__ void record_panel_kernel(const PanelOut *__restrict__ out, const int *__restrict__ idx,
-                                    int r0, int z0, int *piv_all, uint32_t *d_all,
-                                    uint32_t *e_all, int *zero_all, int *zero_cols)
-{
-    const int np = out->np, nz = out->nzero;
-    for (int k = threadIdx.x; k < np; k += blockDim.x) {
-        piv_all[r0 + k] = idx[out->piv_rows[k]];
-        d_all[r0 + k] = out->dval[k];
-        e_all[r0 + k] = out->eval[k];
-    }
-    for (int q = threadIdx.x; q < nz; q += blockDim.x) {
-        zero_all[z0 + q] = idx[out->zero_rows[q]];
-        zero_cols[z0 + q] = r0 + out->zero_np[q];  // L columns that existed when it was found zero
     }
 }
 
@@ -124,13 +98,15 @@ __global__ void __launch_bounds__(256) finalize_kernel(int64_t n, const uint32_t
                                                        const uint32_t *__restrict__ d_all,
                                                        const uint32_t *__restrict__ e_all,
                                                        const int *__restrict__ zero_all,
-                                                       const int *__restrict__ zero_cols, int r,
+                                                       const int *__restrict__ zero_cols,
+                                                       const LoopState *__restrict__ ls,
                                                        uint32_t *__restrict__ A, int64_t lda,
                                                        int32_t *__restrict__ perm, uint32_t *__restrict__ e,
                                                        int64_t *__restrict__ rank, int vec)
 {
     const int64_t k = blockIdx.x;
-    if (k >= n) return;
+    if (k >= n || ls->aborted) return;  // an aborted factorisation leaves the outputs alone
+    const int r = ls->r0;
     const int src = (k < r) ? piv_all[k] : zero_all[k - r];
     if (threadIdx.x == 0) {
         perm[k] = src;
@@ -167,6 +143,58 @@ __global__ void __launch_bounds__(256) finalize_kernel(int64_t n, const uint32_t
         else if (c < cmax) v = __ldg(lrow + c);
         else v = 0u;
         arow[c] = v;
+    }
+}
+
+// Start (init) or advance the panel loop; see launch_loop_step.  Block 0
+// updates the state; every block clears its share of the next panel's
+// scratch, sized from the panel record alone (never from the state block 0
+// is writing).
+__global__ void __launch_bounds__(256) loop_step_kernel(LoopState *ls, const PanelOut *out, int init, int64_t n,
+                                                        int32_t *status, uint32_t *LpT, int64_t ldL,
+                                                        uint8_t *consumed, PanelSync *sync,
+                                                        cudaGraphConditionalHandle cond, int set_cond)
+{
+    const int mclr = init ? (int)n : (out->abort ? 0 : out->m_next);
+    const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (mclr > 0) {
+        if ((ldL & 3) == 0) {
+            // rows of LpT start on 16-byte boundaries: clear [0, round_up(m, 4)) of each
+            const int64_t q4 = ((int64_t)mclr + 3) >> 2, total = q4 * KP_MAX;
+            for (int64_t q = tid; q < total; q += nthr) {
+                const int64_t k = q / q4, c = q - k * q4;
+                reinterpret_cast<uint4 *>(LpT + k * ldL)[c] = make_uint4(0, 0, 0, 0);
+            }
+        } else {
+            const int64_t total = (int64_t)mclr * KP_MAX;
+            for (int64_t q = tid; q < total; q += nthr) LpT[(q / mclr) * ldL + q % mclr] = 0u;
+        }
+        for (int64_t t = tid; t < mclr; t += nthr) consumed[t] = 0;
+    }
+    if (blockIdx.x != 0) return;
+    if (threadIdx.x == 0) {
+        *sync = PanelSync{0, 0, 0, 0};
+        if (init) {
+            *ls = LoopState{(int)n, 0, 0, 0, 0, 0, {0, 0}};
+        } else if (!ls->done) {
+            ls->npanel += 1;
+            if (out->abort || *(volatile int32_t *)status != 0) {
+                ls->done = 1;
+                ls->aborted = 1;
+            } else if (out->m_next >= ls->m) {
+                // a panel always retires a row; this guard keeps the loop finite
+                atomicCAS(status, 0, LDLT_ERR_INTERNAL);
+                ls->done = 1;
+                ls->aborted = 1;
+            } else {
+                ls->r0 += out->np;
+                ls->z0 += out->nzero;
+                ls->m = out->m_next;
+                if (out->m_next == 0) ls->done = 1;
+            }
+        }
+        if (set_cond) cudaGraphSetConditional(cond, ls->done ? 0u : 1u);
     }
 }
 
@@ -221,40 +249,37 @@ cudaError_t launch_ingest_perm(const uint32_t *A, int64_t lda, int64_t n, const 
     return cudaGetLastError();
 }
 
-cudaError_t launch_lw_scatter(const uint32_t *LpT, int64_t ldL, int m, int np, const int *idx,
-                              uint32_t *Lw, int64_t ldw, int col0, cudaStream_t st)
+cudaError_t launch_lw_scatter(const uint32_t *LpC, int64_t ldL, int64_t n, const LoopState *ls,
+                              const PanelOut *out, const int *idx, uint32_t *Lw, int64_t ldw,
+                              cudaStream_t st)
 {
-    if (m == 0 || np == 0) return cudaSuccess;
-    dim3 grid((m + 31) / 32, (np + 31) / 32);
-    lw_scatter_kernel<<<grid, dim3(32, 8), 0, st>>>(LpT, ldL, m, np, idx, Lw, ldw, col0);
+    if (n == 0) return cudaSuccess;
+    dim3 grid((unsigned)((n + 31) / 32), KP_MAX / 32);
+    lw_scatter_kernel<<<grid, dim3(32, 8), 0, st>>>(LpC, ldL, ls, out, idx, Lw, ldw);
     return cudaGetLastError();
 }
 
-cudaError_t launch_compact_copy(const uint32_t *S, int64_t ldS, const int *sigma, int m_next,
-                                uint32_t *Snext, cudaStream_t st)
+cudaError_t launch_loop_step(LoopState *ls, const PanelOut *out, int init, int64_t n, int32_t *status,
+                             uint32_t *LpT, int64_t ldL, uint8_t *consumed, PanelSync *sync,
+                             cudaGraphConditionalHandle cond, int set_cond, int num_sms, cudaStream_t st)
 {
-    if (m_next == 0) return cudaSuccess;
-    dim3 grid(gx_for(m_next, 256), (unsigned)m_next);
-    compact_copy_kernel<<<grid, 256, 0, st>>>(S, ldS, sigma, m_next, Snext);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_record_panel(const PanelOut *out, const int *idx, int r0, int z0, int *piv_all,
-                                uint32_t *d_all, uint32_t *e_all, int *zero_all, int *zero_cols,
-                                cudaStream_t st)
-{
-    record_panel_kernel<<<1, 256, 0, st>>>(out, idx, r0, z0, piv_all, d_all, e_all, zero_all, zero_cols);
+    // about one 16-byte store per thread per clear of an n-row panel
+    int64_t g = ((n + 3) / 4 * KP_MAX + 255) / 256;
+    if (g > 2 * num_sms) g = 2 * num_sms;
+    if (g < 1) g = 1;
+    loop_step_kernel<<<(unsigned)g, 256, 0, st>>>(ls, out, init, n, status, LpT, ldL, consumed, sync, cond,
+                                                  set_cond);
     return cudaGetLastError();
 }
 
 cudaError_t launch_finalize(int64_t n, const uint32_t *Lw, int64_t ldw, const int *piv_all,
                             const uint32_t *d_all, const uint32_t *e_all, const int *zero_all,
-                            const int *zero_cols, int r, uint32_t *A, int64_t lda, int32_t *perm,
-                            uint32_t *e, int64_t *rank, cudaStream_t st)
+                            const int *zero_cols, const LoopState *ls, uint32_t *A, int64_t lda,
+                            int32_t *perm, uint32_t *e, int64_t *rank, cudaStream_t st)
 {
     if (n == 0) return cudaSuccess;
     const int vec = ((uintptr_t)A % 16 == 0) && (lda % 4 == 0) && (ldw % 4 == 0);
-    finalize_kernel<<<(unsigned)n, 256, 0, st>>>(n, Lw, ldw, piv_all, d_all, e_all, zero_all, zero_cols, r,
+    finalize_kernel<<<(unsigned)n, 256, 0, st>>>(n, Lw, ldw, piv_all, d_all, e_all, zero_all, zero_cols, ls,
                                                  A, lda, perm, e, rank, vec);
     return cudaGetLastError();
 }

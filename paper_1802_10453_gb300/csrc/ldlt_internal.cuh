@@ -26,7 +26,7 @@ constexpr int EV_REC = 8 + EV_WORDS;  // event record: header (one Event) then p
 // every row starts on a 256-byte boundary.
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
-enum EventKind : int { EV_PIVOT1 = 1, EV_PIVOT2 = 2, EV_SCAN = 3, EV_END = 4, EV_FARPAIR = 5 };
+enum EventKind : int { EV_PIVOT1 = 1, EV_PIVOT2 = 2, EV_SCAN = 3, EV_END = 4 };
 
 // One message from the leader CTA to the helper CTAs (see panel.cu).
 struct Event {
@@ -34,9 +34,9 @@ struct Event {
     int a, b;        // compact rows of the pivot (b only for 2x2)
     int np;          // length of the z vectors (storage columns they cover)
     uint32_t s0;     // the scale W of the division-free Crout form
-    int col;         // storage column the event writes (pivots, far pair)
-    int scan_id;     // EV_SCAN: scan id; EV_FARPAIR: the far pair's own scan
-    int aux;         // EV_FARPAIR: corrections | re-issued scans << 16
+    int col;         // storage column the event writes (pivots), else -1
+    int scan_id;     // EV_SCAN: scan id
+    int aux;         // unused (zero)
 };
 
 // Counters the CTAs of one panel launch share (zeroed before the launch).
@@ -57,8 +57,8 @@ struct ScanSlot {
 };
 static_assert(MAX_PANEL_GRID <= 8 * 32, "one answer bit per helper CTA");
 
-// What the panel kernel reports back to the host.  Pivots, D and the L
-// columns (LpC) are in pivot order.
+// What the panel kernel reports to the kernels that follow it.  Pivots, D
+// and the L columns (LpC) are in pivot order.
 struct PanelOut {
     int np;          // pivots taken in this panel (L columns)
     int nzero;       // non-pivot rows found
@@ -69,20 +69,39 @@ struct PanelOut {
     int pad[2];
     long long cyc[8];       // unused (zero)
     long long dbg[16];      // pivot-chain counters (see ldlt_rpm_profile_read)
-    int piv_rows[KP_MAX];   // compact rows, pivot order
     uint32_t dval[KP_MAX];  // D diagonal
     uint32_t eval[KP_MAX];  // x at a 2x2 block start, else 0
-    int zero_rows[W0];      // compact rows, ascending
-    int zero_np[W0];        // pivots of this panel taken before each zero row
 };
+
+// State of the panel loop, in device memory: every kernel of a panel step
+// reads its sizes here and in PanelOut, so the whole loop is enqueued (a
+// CUDA graph with a device-side while condition) without the host reading
+// anything back.
+struct LoopState {
+    int m;           // order of the current Schur complement
+    int r0;          // pivots (L columns) taken by earlier panels
+    int z0;          // non-pivot rows found by earlier panels
+    int done;        // 1 once the factorisation has ended (finished or aborted)
+    int aborted;     // 1 if it ended on an error (status holds the code)
+    int npanel;      // panels run
+    int pad[2];
+};
+
+// Helper CTAs a panel over m rows uses, at most `cap` (the launched grid).
+__host__ __device__ inline int panel_grid(int m, int cap)
+{
+    const int w = m < W0 ? m : W0;
+    if (m <= w) return 1;
+    const int need = 1 + (m - w + MIN_HELPER_ROWS - 1) / MIN_HELPER_ROWS;
+    return need < cap ? need : cap;
+}
 
 struct PanelParams {
     const uint32_t *S;      // compact Schur complement, lower triangle, ldS
     int64_t ldS;
-    int m;
+    const LoopState *ls;    // m = ls->m rows, window min(W0, m)
     FieldP f;
     int kp;                 // pivot budget of this panel (<= KP_MAX)
-    int w;                  // window rows min(W0, m)
     uint32_t *LpT;          // LpT[k * ldL + t]: scaled Schur column k (storage order) of compact row t
     uint32_t *LpC;          // LpC[k * ldL + t]: L entry of compact row t, pivot-order column k (output)
     int64_t ldL;
@@ -92,6 +111,12 @@ struct PanelParams {
     int *idx_next;          // [m]: out, original index of new compact row
     PanelOut *out;
     PanelSync *sync;
+    // the factorisation's lists, appended at ls->r0 / ls->z0 (original indices)
+    int *piv_all;           // pivot rows, pivot order
+    uint32_t *d_all;        // D
+    uint32_t *e_all;        // x at a 2x2 block start, else 0
+    int *zero_all;          // non-pivot rows
+    int *zero_cols;         // L columns that existed when each was found zero
     uint32_t *evlog;        // [MAX_EVENTS][EV_REC] event records
     ScanSlot *scans;        // [MAX_SCANS]
     uint32_t *partner_lp;   // [SCAN_RING][MAX_PANEL_GRID][PSTR]: candidate rows per scan
@@ -114,38 +139,69 @@ int factor_core(int64_t n, uint32_t p, uint32_t *A, int64_t lda, int32_t *perm, 
                 int32_t *status, int path, void *ws, size_t ws_bytes, void *stream, const int32_t *gperm,
                 int *gbad);
 cudaError_t launch_panel(const PanelParams &pp, int grid, cudaStream_t st);
-cudaError_t launch_lw_scatter(const uint32_t *LpT, int64_t ldL, int m, int np, const int *idx,
-                              uint32_t *Lw, int64_t ldw, int col0, cudaStream_t st);
-cudaError_t launch_compact_copy(const uint32_t *S, int64_t ldS, const int *sigma, int m_next,
-                                uint32_t *Snext, cudaStream_t st);
-cudaError_t launch_record_panel(const PanelOut *out, const int *idx, int r0, int z0,
-                                int *piv_all, uint32_t *d_all, uint32_t *e_all, int *zero_all,
-                                int *zero_cols, cudaStream_t st);
+// The per-panel kernels below size themselves from LoopState / PanelOut;
+// their grids are fixed for order n and surplus CTAs return at once.
+cudaError_t launch_lw_scatter(const uint32_t *LpC, int64_t ldL, int64_t n, const LoopState *ls,
+                              const PanelOut *out, const int *idx, uint32_t *Lw, int64_t ldw,
+                              cudaStream_t st);
+// init != 0: start the loop at order n.  Otherwise advance it past the panel
+// in `out` (end it when nothing remains, on an abort, on an error status, or
+// if a panel retired no row), and, with set_cond, set the graph's while
+// condition to "not done".  Either way the next panel's LpT columns,
+// consumed flags and PanelSync are cleared.
+cudaError_t launch_loop_step(LoopState *ls, const PanelOut *out, int init, int64_t n, int32_t *status,
+                             uint32_t *LpT, int64_t ldL, uint8_t *consumed, PanelSync *sync,
+                             cudaGraphConditionalHandle cond, int set_cond, int num_sms, cudaStream_t st);
 cudaError_t launch_finalize(int64_t n, const uint32_t *Lw, int64_t ldw, const int *piv_all,
                             const uint32_t *d_all, const uint32_t *e_all, const int *zero_all,
-                            const int *zero_cols, int r, uint32_t *A, int64_t lda, int32_t *perm,
-                            uint32_t *e, int64_t *rank, cudaStream_t st);
+                            const int *zero_cols, const LoopState *ls, uint32_t *A, int64_t lda,
+                            int32_t *perm, uint32_t *e, int64_t *rank, cudaStream_t st);
 cudaError_t launch_rpm(int64_t n, const int32_t *perm, const uint32_t *e, const int64_t *rank,
                        int32_t *rpm_col, cudaStream_t st);
 
 // FP64 form of the level-3 update.
 size_t fp64_operand_bytes(int64_t n);
-cudaError_t launch_split_fp64(const uint32_t *LpT, int64_t ldL, const int *sigma, int m_next,
-                              int np, const PanelOut *out, FieldP f, double *GDT, double *GT,
-                              int64_t ldg, int kpad, cudaStream_t st);
-cudaError_t launch_syrdk_fp64(const uint32_t *S, int64_t ldS, const int *sigma, int m_next,
-                              const double *GDT, const double *GT, int64_t ldg, int kpad,
-                              FieldP f, uint32_t *Snext, cudaStream_t st);
+// The operand split kernels also do the update of a panel without pivots:
+// Snext[i][j] = S[sigma i][sigma j] (rows dropped, nothing subtracted).
+cudaError_t launch_split_fp64(const uint32_t *LpC, int64_t ldL, const int *sigma, int64_t n,
+                              const LoopState *ls, const PanelOut *out, FieldP f, double *GDT,
+                              double *GT, int64_t ldg, const uint32_t *S, int64_t ldS, uint32_t *Snext,
+                              cudaStream_t st);
+cudaError_t launch_syrdk_fp64(const uint32_t *S, int64_t ldS, const int *sigma, int64_t n,
+                              const LoopState *ls, const PanelOut *out, const double *GDT,
+                              const double *GT, int64_t ldg, FieldP f, uint32_t *Snext,
+                              cudaStream_t st);
 
 // Tensor-core form of the level-3 update.
 int tc_limbs(uint32_t p);
 int tc_limbs_a(uint32_t p, int *shift);
 int tc_bn(int limbs);
 size_t tc_operand_bytes(int64_t n, int limbs);
-cudaError_t launch_split_tc(const uint32_t *LpT, int64_t ldL, const int *sigma, int m_next,
-                            int np, const PanelOut *out, FieldP f, int limbs, int kpad,
-                            void *Aop, void *Bop, cudaStream_t st);
-cudaError_t launch_syrdk_tc(const uint32_t *S, int64_t ldS, const int *sigma, int m_next,
-                            const void *Aop, const void *Bop, int limbs, int kpad, FieldP f,
-                            uint32_t *Snext, int64_t budget_ns, int32_t *status, int num_sms,
-                            int test_drop, cudaStream_t st);
+cudaError_t launch_split_tc(const uint32_t *LpC, int64_t ldL, const int *sigma, int64_t n,
+                            const LoopState *ls, const PanelOut *out, FieldP f, int limbs,
+                            void *Aop, void *Bop, const uint32_t *S, int64_t ldS, uint32_t *Snext,
+                            cudaStream_t st);
+cudaError_t launch_syrdk_tc(const uint32_t *S, int64_t ldS, const int *sigma, const LoopState *ls,
+                            const PanelOut *out, const void *Aop, const void *Bop, int limbs,
+                            FieldP f, uint32_t *Snext, int64_t budget_ns, int32_t *status,
+                            int num_sms, int test_drop, cudaStream_t st);
+
+// A panel step is live while the loop has not ended and its panel did not
+// abort; the kernels after the panel do nothing otherwise.
+__device__ __forceinline__ bool step_live(const LoopState *ls, const PanelOut *out)
+{
+    return !ls->done && !out->abort;
+}
+
+// Snext[i][j] = S[sigma i][sigma j], j <= i < m_next, for a panel without
+// pivots; CTA b of nb takes rows b, b + nb, ...
+__device__ __forceinline__ void compact_rows(const uint32_t *__restrict__ S, int64_t ldS,
+                                             const int *__restrict__ sigma, int m_next,
+                                             uint32_t *__restrict__ Snext, int b, int nb)
+{
+    for (int i = b; i < m_next; i += nb) {
+        const uint32_t *src = S + (int64_t)sigma[i] * ldS;
+        uint32_t *dst = Snext + (int64_t)i * ldS;
+        for (int j = threadIdx.x; j <= i; j += blockDim.x) dst[j] = src[sigma[j]];
+    }
+}

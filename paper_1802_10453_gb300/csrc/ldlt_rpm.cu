@@ -4,16 +4,23 @@
 // pivot order, Algorithm 2's level-3 updates):
 //   ingest:   S = lower(A) mod p, compact index = original index
 //   repeat:   panel   -- pivot chain over the first W0 rows of S (panel.cu):
-//                        up to KP_MAX pivots, their L columns for every row
-//             record  -- append pivots / D / zero rows to the global lists
+//                        up to KP_MAX pivots, their L columns for every row;
+//                        pivots, D and zero rows appended to the global lists
 //             store   -- L columns into Lw (by original row)
 //             update  -- S <- S[sigma, sigma] - G D G^T on the remaining rows
 //                        (SYRDK, FP64 or tensor-core form), rows compacted
 //   finalize: A <- L in perm order with D on the diagonal (PERM)
-// After each panel three words are read back to size the next launches.
+// The loop runs on the device: every kernel of a panel step reads its sizes
+// from the loop state and the panel record in device memory, and the steps
+// are one CUDA graph whose while node repeats them until the loop state says
+// the factorisation has ended.  A call enqueues that graph (built on the
+// first call with the same arguments, then reused) and returns; nothing is
+// read back.  With profiling on, the same kernels are launched from a host
+// loop that reads the record after each panel to time the phases.
 #include <cstddef>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include "../../include/ldlt_rpm.h"
 #include "ldlt_internal.cuh"
@@ -28,8 +35,7 @@ int g_test_drop = 0;  // failure-detection tests: LDLT_TEST_DROP_*
 struct Prof {
     bool on = false;
     double acc[32] = {};
-    cudaEvent_t evs[2][4] = {};  // two sets: panel i uses set i & 1
-    int pending = -1;            // set whose events are recorded but not yet read
+    cudaEvent_t ev[4] = {};  // panel start, after the panel, after the operand split, step end
     bool ready = false;
 };
 Prof g_prof;
@@ -37,19 +43,16 @@ Prof g_prof;
 void prof_init()
 {
     if (!g_prof.ready) {
-        for (auto &s : g_prof.evs)
-            for (auto &e : s) cudaEventCreate(&e);
+        for (auto &e : g_prof.ev) cudaEventCreate(&e);
         g_prof.ready = true;
     }
 }
 
-// Accumulate the phase times of the last recorded panel (its events have
-// completed: the caller synchronised the stream after them).
+// Accumulate the phase times of the panel step just completed (the caller
+// synchronised the stream after its last event).
 void prof_collect()
 {
-    if (g_prof.pending < 0) return;
-    cudaEvent_t *ev = g_prof.evs[g_prof.pending];
-    cudaEventSynchronize(ev[3]);
+    cudaEvent_t *ev = g_prof.ev;
     float t01 = 0, t12 = 0, t23 = 0;
     cudaEventElapsedTime(&t01, ev[0], ev[1]);
     cudaEventElapsedTime(&t12, ev[1], ev[2]);
@@ -57,7 +60,6 @@ void prof_collect()
     g_prof.acc[0] += t01;
     g_prof.acc[1] += t12;
     g_prof.acc[2] += t23;
-    g_prof.pending = -1;
 }
 
 uint64_t mulmod64(uint64_t a, uint64_t b, uint64_t m) { return (uint64_t)((unsigned __int128)a * b % m); }
@@ -110,10 +112,9 @@ int fp64_kred(uint32_t p)
 struct Layout {
     int64_t ldS;
     size_t S0, S1, Lw, LpT, LpC, idx0, idx1, sigma, consumed, piv_all, d_all, e_all, zero_all, zero_cols;
-    size_t out, sync, evlog, scans, partner_lp, scancol, zlog, opA, opB, total;
+    size_t out, sync, loop, evlog, scans, partner_lp, scancol, zlog, opA, opB, total;
 };
 
-constexpr int MAX_GRID = 1024;
 
 int make_layout(int64_t n, uint32_t p, int path, Layout &L)
 {
@@ -142,6 +143,7 @@ int make_layout(int64_t n, uint32_t p, int path, Layout &L)
     L.zero_cols = take((size_t)nn * 4);
     L.out = take(sizeof(PanelOut));
     L.sync = take(sizeof(PanelSync));
+    L.loop = take(sizeof(LoopState));
     L.evlog = take((size_t)MAX_EVENTS * EV_REC * 4);
     L.scans = take((size_t)MAX_SCANS * sizeof(ScanSlot));
     L.partner_lp = take((size_t)SCAN_RING * MAX_PANEL_GRID * PSTR * 4);
@@ -189,13 +191,11 @@ extern "C" void ldlt_rpm_profile_enable(int on)
 extern "C" void ldlt_rpm_profile_reset(void)
 {
     for (double &a : g_prof.acc) a = 0.0;
-    g_prof.pending = -1;
 }
 
 extern "C" int ldlt_rpm_profile_read(double out[32])
 {
     if (!out) return LDLT_ERR_ARG;
-    prof_collect();
     for (int i = 0; i < 32; ++i) out[i] = g_prof.acc[i];
     return LDLT_OK;
 }
@@ -235,6 +235,297 @@ extern "C" int ldlt_rpm_factor(int64_t n, uint32_t p, uint32_t *A, int64_t lda, 
     return factor_core(n, p, A, lda, perm, e, rank, status, path, ws, ws_bytes, stream, nullptr, nullptr);
 }
 
+namespace {
+
+// Everything the kernels of one factorisation are launched with.  The two
+// halves of a loop iteration run panels from S0 into S1 and back, so each
+// launch's arguments are fixed and the loop can be a graph.
+struct Plan {
+    int64_t n, lda, ldS;
+    uint32_t p;
+    int path, nsm, limbs, pgrid;
+    uint32_t *A;
+    int32_t *perm, *status;
+    uint32_t *e;
+    int64_t *rank;
+    const int32_t *gperm;
+    int *gbad;
+    FieldP f;
+    uint32_t *Sbuf[2], *Lw, *LpT, *LpC;
+    int *idxb[2], *sigma, *piv_all, *zero_all, *zero_cols;
+    uint32_t *d_all, *e_all;
+    uint8_t *consumed, *opA, *opB;
+    PanelOut *out;
+    PanelSync *sync;
+    LoopState *ls;
+    PanelParams pp[2];
+};
+
+void plan_make(Plan &c, int64_t n, uint32_t p, int path, uint32_t *A, int64_t lda, int32_t *perm, uint32_t *e,
+               int64_t *rank, int32_t *status, void *ws, const int32_t *gperm, int *gbad, const Layout &Lo, int nsm)
+{
+    uint8_t *w = (uint8_t *)ws;
+    c.n = n; c.lda = lda; c.ldS = Lo.ldS; c.p = p; c.path = path; c.nsm = nsm;
+    c.limbs = (path == LDLT_PATH_TC) ? tc_limbs(p) : 0;
+    c.A = A; c.perm = perm; c.status = status; c.e = e; c.rank = rank; c.gperm = gperm; c.gbad = gbad;
+    c.f = make_field(p);
+    c.Sbuf[0] = (uint32_t *)(w + Lo.S0);
+    c.Sbuf[1] = (uint32_t *)(w + Lo.S1);
+    c.Lw = (uint32_t *)(w + Lo.Lw);
+    c.LpT = (uint32_t *)(w + Lo.LpT);
+    c.LpC = (uint32_t *)(w + Lo.LpC);
+    c.idxb[0] = (int *)(w + Lo.idx0);
+    c.idxb[1] = (int *)(w + Lo.idx1);
+    c.sigma = (int *)(w + Lo.sigma);
+    c.consumed = w + Lo.consumed;
+    c.piv_all = (int *)(w + Lo.piv_all);
+    c.d_all = (uint32_t *)(w + Lo.d_all);
+    c.e_all = (uint32_t *)(w + Lo.e_all);
+    c.zero_all = (int *)(w + Lo.zero_all);
+    c.zero_cols = (int *)(w + Lo.zero_cols);
+    c.out = (PanelOut *)(w + Lo.out);
+    c.sync = (PanelSync *)(w + Lo.sync);
+    c.ls = (LoopState *)(w + Lo.loop);
+    c.opA = w + Lo.opA;
+    c.opB = c.opA;
+    if (path == LDLT_PATH_TC)
+        c.opB = c.opA + (size_t)round_up(round_up(n, 128) * (int64_t)c.limbs * KP_MAX * 2, 256);
+    // the first panel is the largest: its grid serves every later panel
+    c.pgrid = panel_grid((int)n, nsm < MAX_PANEL_GRID ? nsm : MAX_PANEL_GRID);
+    for (int h = 0; h < 2; ++h) {
+        PanelParams &pp = c.pp[h];
+        pp.S = c.Sbuf[h]; pp.ldS = c.ldS; pp.ls = c.ls; pp.f = c.f; pp.kp = KP_MAX;
+        pp.LpT = c.LpT; pp.LpC = c.LpC; pp.ldL = c.ldS;
+        pp.consumed = c.consumed; pp.idx = c.idxb[h]; pp.sigma = c.sigma; pp.idx_next = c.idxb[h ^ 1];
+        pp.out = c.out; pp.sync = c.sync;
+        pp.piv_all = c.piv_all; pp.d_all = c.d_all; pp.e_all = c.e_all;
+        pp.zero_all = c.zero_all; pp.zero_cols = c.zero_cols;
+        pp.evlog = (uint32_t *)(w + Lo.evlog);
+        pp.scans = (ScanSlot *)(w + Lo.scans);
+        pp.partner_lp = (uint32_t *)(w + Lo.partner_lp);
+        pp.scancol = (uint32_t *)(w + Lo.scancol);
+        pp.zlog = (uint32_t *)(w + Lo.zlog);
+        pp.budget_ns = g_budget_ns; pp.status = status;
+        pp.npend = g_npend;
+        pp.test_drop = g_test_drop;
+    }
+}
+
+// status = 0, S = lower(A) mod p (or P^T A P), loop state at order n
+cudaError_t enqueue_start(const Plan &c, cudaStream_t st)
+{
+    cudaError_t err = cudaMemsetAsync(c.status, 0, sizeof(int32_t), st);
+    if (err != cudaSuccess) return err;
+    err = c.gperm ? launch_ingest_perm(c.A, c.lda, c.n, c.gperm, c.Sbuf[0], c.ldS, c.idxb[0], c.f, c.gbad, st)
+                  : launch_ingest(c.A, c.lda, c.n, c.Sbuf[0], c.ldS, c.idxb[0], c.f, st);
+    if (err != cudaSuccess) return err;
+    return launch_loop_step(c.ls, c.out, 1, c.n, c.status, c.LpT, c.ldS, c.consumed, c.sync, 0, 0, c.nsm, st);
+}
+
+// One panel step on half h: pivot chain (which also appends to the pivot and
+// zero-row lists), L columns, operand split, level-3 update (the split does
+// the compaction of a panel without pivots), loop advance.  ev (profiling):
+// panel start, panel end, split end, update end.
+cudaError_t enqueue_step(const Plan &c, int h, cudaGraphConditionalHandle cond, int set_cond, cudaEvent_t *ev,
+                         cudaStream_t st)
+{
+#define EQ(call)                                 \
+    do {                                         \
+        cudaError_t _e = (call);                 \
+        if (_e != cudaSuccess) return _e;        \
+    } while (0)
+    if (ev) EQ(cudaEventRecord(ev[0], st));
+    EQ(launch_panel(c.pp[h], c.pgrid, st));
+    if (ev) EQ(cudaEventRecord(ev[1], st));
+    EQ(launch_lw_scatter(c.LpC, c.ldS, c.n, c.ls, c.out, c.idxb[h], c.Lw, c.ldS, st));
+    if (c.path == LDLT_PATH_FP64) {
+        double *GDT = (double *)c.opA;
+        double *GT = GDT + (size_t)KP_MAX * c.ldS;
+        EQ(launch_split_fp64(c.LpC, c.ldS, c.sigma, c.n, c.ls, c.out, c.f, GDT, GT, c.ldS, c.Sbuf[h], c.ldS,
+                             c.Sbuf[h ^ 1], st));
+        if (ev) EQ(cudaEventRecord(ev[2], st));
+        EQ(launch_syrdk_fp64(c.Sbuf[h], c.ldS, c.sigma, c.n, c.ls, c.out, GDT, GT, c.ldS, c.f, c.Sbuf[h ^ 1], st));
+    } else {
+        EQ(launch_split_tc(c.LpC, c.ldS, c.sigma, c.n, c.ls, c.out, c.f, c.limbs, c.opA, c.opB, c.Sbuf[h], c.ldS,
+                           c.Sbuf[h ^ 1], st));
+        if (ev) EQ(cudaEventRecord(ev[2], st));
+        EQ(launch_syrdk_tc(c.Sbuf[h], c.ldS, c.sigma, c.ls, c.out, c.opA, c.opB, c.limbs, c.f, c.Sbuf[h ^ 1],
+                           g_budget_ns, c.status, c.nsm, g_test_drop == LDLT_TEST_DROP_UPDATE_COPIES, st));
+    }
+    if (ev) EQ(cudaEventRecord(ev[3], st));
+    EQ(launch_loop_step(c.ls, c.out, 0, c.n, c.status, c.LpT, c.ldS, c.consumed, c.sync, cond, set_cond, c.nsm,
+                        st));
+    return cudaSuccess;
+#undef EQ
+}
+
+cudaError_t enqueue_finish(const Plan &c, cudaStream_t st)
+{
+    return launch_finalize(c.n, c.Lw, c.ldS, c.piv_all, c.d_all, c.e_all, c.zero_all, c.zero_cols, c.ls, c.A,
+                           c.lda, c.perm, c.e, c.rank, st);
+}
+
+// Profiling: the same kernels from a host loop, one readback per panel.
+int run_profiled(const Plan &c, cudaStream_t st)
+{
+    CK(enqueue_start(c, st));
+    g_prof.acc[5] += 2;  // ingest, loop start
+    for (int ipanel = 0;; ++ipanel) {
+        CK(enqueue_step(c, ipanel & 1, 0, 0, g_prof.ev, st));
+        struct { int h[8]; long long cyc[8]; long long dbg[16]; } rb;
+        static_assert(offsetof(PanelOut, cyc) == 8 * sizeof(int), "PanelOut layout");
+        LoopState lh;
+        CK(cudaMemcpyAsync(&rb, c.out, sizeof(rb), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(&lh, c.ls, sizeof(lh), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        prof_collect();
+        const int *hdr = rb.h;
+        const int np = hdr[0], m_next = hdr[3];
+        g_prof.acc[5] += 5;  // panel, L scatter, split, update, loop step
+        g_prof.acc[6] += 1;
+        g_prof.acc[7] += hdr[5];
+        for (int i = 0; i < 8; ++i) g_prof.acc[8 + i] += (double)rb.cyc[i];
+        for (int i = 0; i < 16; ++i) g_prof.acc[16 + i] += (double)rb.dbg[i];
+        if (!hdr[4] && np > 0 && m_next > 0) {
+            g_prof.acc[3] += (double)m_next * (double)(m_next + 1) * 0.5 * (double)np;
+            g_prof.acc[4] += 1;
+        }
+        if (lh.done) break;
+    }
+    CK(enqueue_finish(c, st));
+    g_prof.acc[5] += 1;
+    return LDLT_OK;
+}
+
+cudaError_t build_graph(const Plan &c, cudaGraphExec_t *exec)
+{
+    cudaStream_t cs = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaError_t err = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (err != cudaSuccess) return err;
+    err = cudaGraphCreate(&g, 0);
+    auto fail = [&](cudaError_t e2) {
+        cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(cs, &cst) == cudaSuccess && cst != cudaStreamCaptureStatusNone) {
+            cudaGraph_t junk = nullptr;
+            cudaStreamEndCapture(cs, &junk);
+        }
+        if (g) cudaGraphDestroy(g);
+        cudaStreamDestroy(cs);
+        return e2;
+    };
+    if (err != cudaSuccess) return fail(err);
+    // start: status, ingest, loop state
+    err = cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (err != cudaSuccess) return fail(err);
+    err = enqueue_start(c, cs);
+    if (err != cudaSuccess) return fail(err);
+    cudaStreamCaptureStatus cst;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    err = cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &deps, nullptr, &ndeps);
+    if (err != cudaSuccess) return fail(err);
+    cudaGraphNode_t dep[8];
+    if (ndeps > 8) return fail(cudaErrorUnknown);
+    for (size_t i = 0; i < ndeps; ++i) dep[i] = deps[i];
+    cudaGraph_t tmp = nullptr;
+    err = cudaStreamEndCapture(cs, &tmp);
+    if (err != cudaSuccess) return fail(err);
+    // the panel loop: a while node, condition set by the second half's loop step
+    cudaGraphConditionalHandle cond;
+    err = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault);
+    if (err != cudaSuccess) return fail(err);
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t loop;
+    err = cudaGraphAddNode(&loop, g, dep, nullptr, ndeps, &cp);
+    if (err != cudaSuccess) return fail(err);
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    err = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (err != cudaSuccess) return fail(err);
+    err = enqueue_step(c, 0, cond, 0, nullptr, cs);
+    if (err == cudaSuccess) err = enqueue_step(c, 1, cond, 1, nullptr, cs);
+    if (err != cudaSuccess) return fail(err);
+    err = cudaStreamEndCapture(cs, &tmp);
+    if (err != cudaSuccess) return fail(err);
+    // finish: L in perm order, D, perm, e, rank
+    err = cudaStreamBeginCaptureToGraph(cs, g, &loop, nullptr, 1, cudaStreamCaptureModeRelaxed);
+    if (err != cudaSuccess) return fail(err);
+    err = enqueue_finish(c, cs);
+    if (err != cudaSuccess) return fail(err);
+    err = cudaStreamEndCapture(cs, &tmp);
+    if (err != cudaSuccess) return fail(err);
+    err = cudaGraphInstantiate(exec, g, 0);
+    cudaGraphDestroy(g);
+    g = nullptr;
+    cudaStreamDestroy(cs);
+    return err;
+}
+
+// Instantiated graphs by their launch arguments (every pointer and size the
+// kernels are given), least recently used first out.  Each entry keeps an
+// event recorded after its last launch: an entry is destroyed only after
+// that launch has finished.
+struct GraphKey {
+    int64_t n, lda;
+    uint32_t p;
+    int path, dev, nsm, npend, test_drop;
+    int64_t budget;
+    const void *A, *perm, *e, *rank, *status, *ws, *gperm, *gbad;
+};
+struct GraphEntry {
+    GraphKey key;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t done = nullptr;
+    uint64_t used = 0;
+};
+constexpr int GRAPH_CACHE = 4;
+std::mutex g_graph_mu;
+GraphEntry g_graphs[GRAPH_CACHE];
+uint64_t g_graph_clock = 0;
+
+int run_graph(const Plan &c, cudaStream_t st)
+{
+    GraphKey k;
+    std::memset(&k, 0, sizeof(k));
+    k.n = c.n; k.lda = c.lda; k.p = c.p; k.path = c.path; k.nsm = c.nsm;
+    k.npend = g_npend; k.test_drop = g_test_drop; k.budget = g_budget_ns;
+    CK(cudaGetDevice(&k.dev));
+    k.A = c.A; k.perm = c.perm; k.e = c.e; k.rank = c.rank; k.status = c.status;
+    k.ws = c.Sbuf[0]; k.gperm = c.gperm; k.gbad = c.gbad;
+    std::lock_guard<std::mutex> lock(g_graph_mu);
+    GraphEntry *hit = nullptr, *lru = &g_graphs[0];
+    for (GraphEntry &ge : g_graphs) {
+        if (ge.exec && std::memcmp(&ge.key, &k, sizeof(k)) == 0) { hit = &ge; break; }
+        if (!ge.exec || (lru->exec && ge.used < lru->used)) lru = &ge;
+    }
+    if (!hit) {
+        cudaGraphExec_t ex = nullptr;
+        CK(build_graph(c, &ex));
+        if (lru->exec) {
+            cudaEventSynchronize(lru->done);  // its last launch has finished
+            cudaGraphExecDestroy(lru->exec);
+            lru->exec = nullptr;
+        }
+        if (!lru->done && cudaEventCreateWithFlags(&lru->done, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGraphExecDestroy(ex);
+            return LDLT_ERR_CUDA;
+        }
+        std::memcpy(&lru->key, &k, sizeof(k));
+        lru->exec = ex;
+        hit = lru;
+    }
+    hit->used = ++g_graph_clock;
+    CK(cudaGraphLaunch(hit->exec, st));
+    CK(cudaEventRecord(hit->done, st));
+    return LDLT_OK;
+}
+
+}  // namespace
+
 int factor_core(int64_t n, uint32_t p, uint32_t *A, int64_t lda, int32_t *perm, uint32_t *e, int64_t *rank,
                 int32_t *status, int path, void *ws, size_t ws_bytes, void *stream, const int32_t *gperm,
                 int *gbad)
@@ -256,131 +547,16 @@ int factor_core(int64_t n, uint32_t p, uint32_t *A, int64_t lda, int32_t *perm, 
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     if (major != 10 || minor != 3) return LDLT_ERR_NO_DEVICE;
 
-    CK(cudaMemsetAsync(status, 0, sizeof(int32_t), st));
     if (n == 0) {
+        CK(cudaMemsetAsync(status, 0, sizeof(int32_t), st));
         CK(cudaMemsetAsync(rank, 0, sizeof(int64_t), st));
         return LDLT_OK;
     }
 
-    uint8_t *w = (uint8_t *)ws;
-    uint32_t *Sbuf[2] = {(uint32_t *)(w + Lo.S0), (uint32_t *)(w + Lo.S1)};
-    uint32_t *Lw = (uint32_t *)(w + Lo.Lw);
-    uint32_t *LpT = (uint32_t *)(w + Lo.LpT);
-    uint32_t *LpC = (uint32_t *)(w + Lo.LpC);
-    int *idxb[2] = {(int *)(w + Lo.idx0), (int *)(w + Lo.idx1)};
-    int *sigma = (int *)(w + Lo.sigma);
-    uint8_t *consumed = w + Lo.consumed;
-    int *piv_all = (int *)(w + Lo.piv_all);
-    uint32_t *d_all = (uint32_t *)(w + Lo.d_all);
-    uint32_t *e_all = (uint32_t *)(w + Lo.e_all);
-    int *zero_all = (int *)(w + Lo.zero_all);
-    int *zero_cols = (int *)(w + Lo.zero_cols);
-    PanelOut *out = (PanelOut *)(w + Lo.out);
-    PanelSync *sync = (PanelSync *)(w + Lo.sync);
-    const int64_t ldS = Lo.ldS;
-    const FieldP f = make_field(p);
-    const int limbs = (path == LDLT_PATH_TC) ? tc_limbs(p) : 0;
-
-    if (gperm) CK(launch_ingest_perm(A, lda, n, gperm, Sbuf[0], ldS, idxb[0], f, gbad, st));
-    else CK(launch_ingest(A, lda, n, Sbuf[0], ldS, idxb[0], f, st));
-    const bool prof = g_prof.on;
-    if (prof) g_prof.acc[5] += 1;
-
-    int m = (int)n, r0 = 0, z0 = 0, cur = 0, ipanel = 0;
-    while (m > 0) {
-        cudaEvent_t *ev = g_prof.evs[ipanel & 1];
-        CK(cudaMemset2DAsync(LpT, (size_t)ldS * 4, 0, (size_t)m * 4, KP_MAX, st));
-        CK(cudaMemsetAsync(consumed, 0, (size_t)m, st));
-        CK(cudaMemsetAsync(sync, 0, sizeof(PanelSync), st));
-
-        PanelParams pp;
-        pp.S = Sbuf[cur]; pp.ldS = ldS; pp.m = m; pp.f = f;
-        pp.kp = KP_MAX; pp.w = m < W0 ? m : W0;
-        pp.LpT = LpT; pp.LpC = LpC; pp.ldL = ldS;
-        pp.consumed = consumed; pp.idx = idxb[cur]; pp.sigma = sigma; pp.idx_next = idxb[cur ^ 1];
-        pp.out = out; pp.sync = sync;
-        pp.evlog = (uint32_t *)(w + Lo.evlog);
-        pp.scans = (ScanSlot *)(w + Lo.scans); pp.partner_lp = (uint32_t *)(w + Lo.partner_lp);
-        pp.scancol = (uint32_t *)(w + Lo.scancol);
-        pp.zlog = (uint32_t *)(w + Lo.zlog);
-        pp.budget_ns = g_budget_ns; pp.status = status;
-        pp.npend = g_npend;
-        pp.test_drop = g_test_drop;
-        int grid = 1;
-        if (m > pp.w) {
-            // spread the far rows over every SM, at least MIN_HELPER_ROWS rows per helper
-            const int need = 1 + (m - pp.w + MIN_HELPER_ROWS - 1) / MIN_HELPER_ROWS;
-            grid = need < nsm ? need : nsm;
-            if (grid > MAX_PANEL_GRID) grid = MAX_PANEL_GRID;
-        }
-        if (prof) CK(cudaEventRecord(ev[0], st));
-        CK(launch_panel(pp, grid, st));
-        CK(launch_record_panel(out, idxb[cur], r0, z0, piv_all, d_all, e_all, zero_all, zero_cols, st));
-        struct { int h[8]; long long cyc[8]; long long dbg[16]; } rb;
-        static_assert(offsetof(PanelOut, cyc) == 8 * sizeof(int), "PanelOut layout");
-        CK(cudaMemcpyAsync(&rb, out, sizeof(rb), cudaMemcpyDeviceToHost, st));
-        const int *hdr = rb.h;
-        if (prof) CK(cudaEventRecord(ev[1], st));
-        CK(cudaStreamSynchronize(st));
-        if (prof) prof_collect();  // the previous panel's events precede this sync
-        const int np = hdr[0], nzero = hdr[1], m_next = hdr[3], aborted = hdr[4];
-        if (prof) {
-            g_prof.acc[5] += 2;  // panel, record
-            g_prof.acc[6] += 1;
-            g_prof.acc[7] += hdr[5];
-            for (int i = 0; i < 8; ++i) g_prof.acc[8 + i] += (double)rb.cyc[i];
-            for (int i = 0; i < 16; ++i) g_prof.acc[16 + i] += (double)rb.dbg[i];
-        }
-        if (aborted) return LDLT_OK;  // LDLT_ERR_TIMEOUT is in *status
-        CK(launch_lw_scatter(LpC, ldS, m, np, idxb[cur], Lw, ldS, r0, st));
-        if (prof && np > 0) g_prof.acc[5] += 1;
-        bool upd = false;
-        if (m_next > 0) {
-            if (np > 0) {
-                const int kpad = (int)round_up(np, 64);
-                if (path == LDLT_PATH_FP64) {
-                    double *GDT = (double *)(w + Lo.opA);
-                    double *GT = GDT + (size_t)KP_MAX * ldS;
-                    CK(launch_split_fp64(LpC, ldS, sigma, m_next, np, out, f, GDT, GT, ldS, kpad, st));
-                    if (prof) CK(cudaEventRecord(ev[2], st));
-                    upd = true;
-                    CK(launch_syrdk_fp64(Sbuf[cur], ldS, sigma, m_next, GDT, GT, ldS, kpad, f,
-                                         Sbuf[cur ^ 1], st));
-                } else {
-                    uint8_t *opA = w + Lo.opA;
-                    const size_t aBytes = (size_t)round_up(round_up(n, 128) * (int64_t)limbs * KP_MAX * 2, 256);
-                    uint8_t *opB = opA + aBytes;
-                    CK(launch_split_tc(LpC, ldS, sigma, m_next, np, out, f, limbs, kpad, opA, opB, st));
-                    if (prof) CK(cudaEventRecord(ev[2], st));
-                    upd = true;
-                    CK(launch_syrdk_tc(Sbuf[cur], ldS, sigma, m_next, opA, opB, limbs, kpad, f,
-                                       Sbuf[cur ^ 1], g_budget_ns, status, nsm,
-                                       g_test_drop == LDLT_TEST_DROP_UPDATE_COPIES, st));
-                }
-            } else {
-                CK(launch_compact_copy(Sbuf[cur], ldS, sigma, m_next, Sbuf[cur ^ 1], st));
-                if (prof) g_prof.acc[5] += 1;
-            }
-        }
-        if (prof) {
-            if (!upd) CK(cudaEventRecord(ev[2], st));
-            CK(cudaEventRecord(ev[3], st));
-            g_prof.pending = ipanel & 1;
-            if (upd) {
-                g_prof.acc[3] += (double)m_next * (double)(m_next + 1) * 0.5 * (double)np;
-                g_prof.acc[4] += 1;
-                g_prof.acc[5] += 2;  // split, update
-            }
-        }
-        r0 += np;
-        z0 += nzero;
-        cur ^= 1;
-        m = m_next;
-        ++ipanel;
-    }
-    CK(launch_finalize(n, Lw, ldS, piv_all, d_all, e_all, zero_all, zero_cols, r0, A, lda, perm, e, rank, st));
-    if (prof) g_prof.acc[5] += 1;
-    return LDLT_OK;
+    Plan pl;
+    plan_make(pl, n, p, path, A, lda, perm, e, rank, status, ws, gperm, gbad, Lo, nsm);
+    if (g_prof.on) return run_profiled(pl, st);
+    return run_graph(pl, st);
 }
 
 extern "C" int rpm_from_factor(int64_t n, const int32_t *perm, const uint32_t *e, const int64_t *rank,

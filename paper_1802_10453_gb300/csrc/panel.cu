@@ -514,13 +514,13 @@ __device__ void helper_cta(const PanelParams &P, Shared &sh, int lo, int hi)
 // leader CTA
 // ---------------------------------------------------------------------------
 template <bool BIG>
-__device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
+__device__ void leader_cta(const PanelParams &P, Shared &sh, const int m, const int nh)
 {
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     const FieldP f = P.f;
-    const int w = P.w;
-    const int nh = gridDim.x - 1;
+    const int w = m < W0 ? m : W0;
+    const bool helpers = nh > 0;
     for (int t = tid; t < W0; t += blockDim.x) sh.wstate[t] = 0;
     for (int i = tid; i < SRING; i += blockDim.x) sh.res_ok[i] = 0;
     if (tid == 0) {
@@ -596,7 +596,7 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
         // the rows below v answered (no smaller row can still come), which
         // is usually well before the last helper is done.
         if (!helpers) return;
-        const int chunk = (P.m - w + nh - 1) / nh;  // far rows per helper, as in helper_cta
+        const int chunk = (m - w + nh - 1) / nh;  // far rows per helper, as in helper_cta
         volatile int *ab = &P.sync->abort;
         int base = 0;
         unsigned posted = 0u;  // bit i: scan base + i posted
@@ -724,7 +724,7 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
             if (resolved(id)) {  // the answer is read only after its flag
                 res = true;
                 v = sh.res_min[id % SRING];
-                hit = v >= w && v < P.m;
+                hit = v >= w && v < m;
             }
         }
         const unsigned rm = __ballot_sync(0xffffffffu, res), hm = __ballot_sync(0xffffffffu, hit);
@@ -893,7 +893,7 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
             // partner found by this row's scan before the rollback
             b = force_b;
             far = true;
-            const int chunk = (P.m - w + nh - 1) / nh;
+            const int chunk = (m - w + nh - 1) / nh;
             const int owner = 1 + (b - w) / chunk;
             const uint32_t *src = P.partner_lp +
                                   ((int64_t)(force_sid % SCAN_RING) * MAX_PANEL_GRID + owner) * PSTR;
@@ -1091,19 +1091,24 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, bool helpers)
     __threadfence();
     cbar();
 
-    // ---- report ----
-    for (int k = tid; k < np; k += NCT) {
-        P.out->piv_rows[k] = sh.piv_rows[k];
-        P.out->dval[k] = sh.dtrue[k];
-        P.out->eval[k] = sh.etrue[k];
-    }
-    for (int q = tid; q < nzero; q += NCT) {
-        P.out->zero_rows[q] = sh.zero_rows[q];
-        P.out->zero_np[q] = sh.zero_np[q];
+    // ---- report: D and x for the update, the pivots and zero rows (as
+    // original indices) appended to the factorisation's lists ----
+    {
+        const int r0 = P.ls->r0, z0 = P.ls->z0;
+        for (int k = tid; k < np; k += NCT) {
+            P.out->dval[k] = sh.dtrue[k];
+            P.out->eval[k] = sh.etrue[k];
+            P.piv_all[r0 + k] = P.idx[sh.piv_rows[k]];
+            P.d_all[r0 + k] = sh.dtrue[k];
+            P.e_all[r0 + k] = sh.etrue[k];
+        }
+        for (int q = tid; q < nzero; q += NCT) {
+            P.zero_all[z0 + q] = P.idx[sh.zero_rows[q]];
+            P.zero_cols[z0 + q] = r0 + sh.zero_np[q];  // L columns that existed when it was found zero
+        }
     }
 
     // ---- compaction of the remaining rows [iend, m) minus consumed partners ----
-    const int m = P.m;
     const int len = m - iend;
     const int per = (len + NCT - 1) / NCT;
     const int lo = iend + tid * per, hi = min(m, lo + per);
@@ -1149,7 +1154,11 @@ __global__ void __launch_bounds__(BLOCK, 1) panel_kernel(PanelParams P)
 {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     Shared &sh = *reinterpret_cast<Shared *>(smem_raw);
-    const bool helpers = gridDim.x > 1;
+    // the loop state was written by earlier kernels: every CTA reads the same
+    if (P.ls->done) return;
+    const int m = P.ls->m;
+    const int ncta = panel_grid(m, gridDim.x);  // the grid is sized for the first panel
+    if (blockIdx.x >= ncta) return;
     if (*(volatile int32_t *)P.status != 0) {
         // an earlier kernel of this factorisation gave up: end it here
         if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -1158,14 +1167,14 @@ __global__ void __launch_bounds__(BLOCK, 1) panel_kernel(PanelParams P)
         }
         return;
     }
+    const int nh = ncta - 1;
     if (blockIdx.x == 0) {
-        leader_cta<BIG>(P, sh, helpers);
+        leader_cta<BIG>(P, sh, m, nh);
     } else {
-        const int nh = gridDim.x - 1;
-        const int far = P.m - P.w;
-        const int chunk = (far + nh - 1) / nh;
-        const int lo = P.w + (blockIdx.x - 1) * chunk;
-        const int hi = min(P.m, lo + chunk);
+        const int w = m < W0 ? m : W0;
+        const int chunk = (m - w + nh - 1) / nh;
+        const int lo = w + (blockIdx.x - 1) * chunk;
+        const int hi = min(m, lo + chunk);
         helper_cta<BIG>(P, sh, lo, hi);
     }
 }
@@ -1182,5 +1191,16 @@ cudaError_t launch_panel(const PanelParams &pp, int grid, cudaStream_t st)
     cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     if (grid <= 1) return cudaLaunchKernel(fn, dim3(1), dim3(BLOCK), args, smem, st);
-    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(BLOCK), args, smem, st);
+    // the CTAs wait on one another: all of them must be resident at once
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(BLOCK);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, fn, args);
 }

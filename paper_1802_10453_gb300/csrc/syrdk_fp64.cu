@@ -22,14 +22,22 @@ __device__ __forceinline__ double bal(uint32_t x, uint32_t p)
     return (double)(x > (p >> 1) ? (int64_t)x - (int64_t)p : (int64_t)x);
 }
 
-// GT[k][i] = G[i][k] = LpT[k][sigma[i]], GDT[k][i] = (G D)[i][k], balanced
-// doubles; rows i >= m_next and columns k >= np are zero.
+// GT[k][i] = G[i][k] = LpC[k][sigma[i]], GDT[k][i] = (G D)[i][k], balanced
+// doubles; rows i >= m_next and columns np <= k < kpad are zero.
 __global__ void split_fp64_kernel(const uint32_t *__restrict__ LpT, int64_t ldL,
-                                  const int *__restrict__ sigma, int m_next, int np,
+                                  const int *__restrict__ sigma, const LoopState *__restrict__ ls,
                                   const PanelOut *__restrict__ out, FieldP f,
                                   double *__restrict__ GDT, double *__restrict__ GT, int64_t ldg,
-                                  int kpad)
+                                  const uint32_t *__restrict__ S, int64_t ldS, uint32_t *__restrict__ Snext)
 {
+    if (!step_live(ls, out)) return;
+    const int m_next = out->m_next, np = out->np;
+    if (np == 0) {
+        compact_rows(S, ldS, sigma, m_next, Snext, blockIdx.y * gridDim.x + blockIdx.x, gridDim.x * gridDim.y);
+        return;
+    }
+    if (m_next == 0) return;
+    const int kpad = (np + 63) / 64 * 64;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int k = blockIdx.y;
     if (i >= (int)ldg || k >= kpad) return;
@@ -59,15 +67,13 @@ __device__ __forceinline__ double red_p(double acc, double p, double pinv)
     return fma(-rint(acc * pinv), p, acc);
 }
 
-// One CTA computes a TB x TB tile (I, J), J <= I, of
-//   Snext[i][j] = S[sigma i][sigma j] - sum_k GD[i][k] G[j][k]   (i >= j).
-__global__ void __launch_bounds__(256) syrdk_fp64_kernel(
-    const uint32_t *__restrict__ S, int64_t ldS, const int *__restrict__ sigma, int m_next,
-    const double *__restrict__ GDT, const double *__restrict__ GT, int64_t ldg, int kpad, int kred,
-    FieldP f, uint32_t *__restrict__ Snext)
+__device__ __forceinline__ void syrdk_fp64_tile(const uint32_t *__restrict__ S, int64_t ldS,
+                                                const int *__restrict__ sigma, int m_next,
+                                                const double *__restrict__ GDT, const double *__restrict__ GT,
+                                                int64_t ldg, int kpad, int kred, FieldP f,
+                                                uint32_t *__restrict__ Snext, int tIdx)
 {
     // triangular tile index -> (I, J)
-    const int tIdx = blockIdx.x;
     int I = (int)((sqrt(8.0 * tIdx + 1.0) - 1.0) * 0.5);
     while ((I + 1) * (I + 2) / 2 <= tIdx) ++I;
     while (I * (I + 1) / 2 > tIdx) --I;
@@ -133,6 +139,24 @@ __global__ void __launch_bounds__(256) syrdk_fp64_kernel(
     }
 }
 
+// A CTA computes TB x TB tiles (I, J), J <= I, grid-strided, of
+//   Snext[i][j] = S[sigma i][sigma j] - sum_k GD[i][k] G[j][k]   (i >= j).
+__global__ void __launch_bounds__(256) syrdk_fp64_kernel(
+    const uint32_t *__restrict__ S, int64_t ldS, const int *__restrict__ sigma,
+    const LoopState *__restrict__ ls, const PanelOut *__restrict__ out,
+    const double *__restrict__ GDT, const double *__restrict__ GT, int64_t ldg, int kred,
+    FieldP f, uint32_t *__restrict__ Snext)
+{
+    if (!step_live(ls, out)) return;
+    const int m_next = out->m_next, np = out->np;
+    if (m_next == 0 || np == 0) return;
+    const int kpad = (np + 63) / 64 * 64;
+    const int nb = (m_next + TB - 1) / TB;
+    const int ntiles = nb * (nb + 1) / 2;
+    for (int tIdx = blockIdx.x; tIdx < ntiles; tIdx += gridDim.x)
+        syrdk_fp64_tile(S, ldS, sigma, m_next, GDT, GT, ldg, kpad, kred, f, Snext, tIdx);
+}
+
 }  // namespace
 
 size_t fp64_operand_bytes(int64_t n)
@@ -141,28 +165,32 @@ size_t fp64_operand_bytes(int64_t n)
     return (size_t)2 * (size_t)KP_MAX * (size_t)ldg * sizeof(double);
 }
 
-cudaError_t launch_split_fp64(const uint32_t *LpT, int64_t ldL, const int *sigma, int m_next,
-                              int np, const PanelOut *out, FieldP f, double *GDT, double *GT,
-                              int64_t ldg, int kpad, cudaStream_t st)
+cudaError_t launch_split_fp64(const uint32_t *LpC, int64_t ldL, const int *sigma, int64_t n,
+                              const LoopState *ls, const PanelOut *out, FieldP f, double *GDT,
+                              double *GT, int64_t ldg, const uint32_t *S, int64_t ldS, uint32_t *Snext,
+                              cudaStream_t st)
 {
-    const int rows = (int)round_up(m_next, TB);
-    dim3 grid((rows + 255) / 256, kpad);
-    split_fp64_kernel<<<grid, 256, 0, st>>>(LpT, ldL, sigma, m_next, np, out, f, GDT, GT, ldg, kpad);
+    if (n == 0) return cudaSuccess;
+    // sized for the largest update (ldg rows, KP_MAX columns); surplus threads return
+    dim3 grid((unsigned)((ldg + 255) / 256), KP_MAX);
+    split_fp64_kernel<<<grid, 256, 0, st>>>(LpC, ldL, sigma, ls, out, f, GDT, GT, ldg, S, ldS, Snext);
     return cudaGetLastError();
 }
 
-cudaError_t launch_syrdk_fp64(const uint32_t *S, int64_t ldS, const int *sigma, int m_next,
-                              const double *GDT, const double *GT, int64_t ldg, int kpad,
-                              FieldP f, uint32_t *Snext, cudaStream_t st)
+cudaError_t launch_syrdk_fp64(const uint32_t *S, int64_t ldS, const int *sigma, int64_t n,
+                              const LoopState *ls, const PanelOut *out, const double *GDT,
+                              const double *GT, int64_t ldg, FieldP f, uint32_t *Snext,
+                              cudaStream_t st)
 {
-    if (m_next == 0) return cudaSuccess;
+    if (n == 0) return cudaSuccess;
     const double h = (double)((f.p - 1) / 2);
     const double lim = 9007199254740992.0 - 1.5 * (double)f.p;  // 2^53 - 1.5p
     int kred = (int)std::floor(lim / (h * h > 1.0 ? h * h : 1.0));
     if (kred > 1 << 20) kred = 1 << 20;
     if (kred < 1) return cudaErrorInvalidValue;
-    const int nb = (m_next + TB - 1) / TB;
-    const unsigned tiles = (unsigned)((int64_t)nb * (nb + 1) / 2);
-    syrdk_fp64_kernel<<<tiles, 256, 0, st>>>(S, ldS, sigma, m_next, GDT, GT, ldg, kpad, kred, f, Snext);
+    const int64_t nb = (n + TB - 1) / TB;
+    int64_t tiles = nb * (nb + 1) / 2;
+    if (tiles > 4096) tiles = 4096;  // grid-strided over the tiles of the current order
+    syrdk_fp64_kernel<<<(unsigned)tiles, 256, 0, st>>>(S, ldS, sigma, ls, out, GDT, GT, ldg, kred, f, Snext);
     return cudaGetLastError();
 }

@@ -23,8 +23,9 @@
 // Kernel structure (one CTA per SM, persistent over the lower-triangle tiles):
 //   warp 0      bulk-copy producer (cp.async.bulk, mbarrier complete_tx)
 //   warp 1      TMEM allocator and MMA issuer (tcgen05.mma, tcgen05.commit)
-//   warps 2..5  epilogue (tcgen05.ld -> recombine -> mod p -> shared tile ->
-//               coalesced read-modify-write of the Schur complement)
+//   warps 2..17 epilogue, two groups of eight warps taking alternate tiles
+//               (tcgen05.ld -> recombine -> mod p -> subtract from the old
+//               values gathered into shared memory -> vector stores)
 // Operands are pre-tiled in HBM by split_tc_kernel so every pipeline stage is
 // one contiguous bulk copy that lands in the no-swizzle K-major "core matrix"
 // layout the tensor core reads (8 rows x 16 bytes per core matrix).
@@ -44,7 +45,8 @@ constexpr int KST = 64;            // K' elements per pipeline stage
 constexpr int STAGE_A = BM * KST * 2;        // 16 KB
 constexpr int STAGE_B_MAX = 256 * KST * 2;   // 32 KB
 constexpr int STAGE_BYTES = STAGE_A + STAGE_B_MAX;
-constexpr int EPI_WARPS = 8;       // two groups of four warps (one per TMEM lane quarter)
+constexpr int EPI_WARPS = 16;      // two groups of eight warps (two per TMEM lane quarter)
+constexpr int GROUP_THREADS = EPI_WARPS / 2 * 32;
 constexpr int EPI_THREADS = EPI_WARPS * 32;
 constexpr int TC_THREADS = 64 + EPI_THREADS;
 constexpr int NST = 3;             // pipeline stages
@@ -173,14 +175,11 @@ __device__ __forceinline__ void cp_async4(uint32_t *dst, const uint32_t *src)
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8])
 {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15])
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
         : "r"(taddr));
 }
 
@@ -212,18 +211,17 @@ struct TcArgs {
     const uint32_t *S;
     int64_t ldS;
     const int *sigma;
-    int m_next;
+    const LoopState *ls;            // with out: m_next rows, K = np (padded to kpad)
+    const PanelOut *out;
     const __nv_bfloat16 *Aop;
     const __nv_bfloat16 *Bop;
-    int limbs, bn, nprime, kprime;  // N' = L_B * bn (limbs = L_B), K' = L_A * kpad
+    int limbs, bn, nprime, la;      // N' = L_B * bn (limbs = L_B), K' = L_A * kpad (la = L_A)
     FieldP f;
     uint64_t bias;                  // multiple of p above 2^50
     uint32_t *Snext;
     int64_t budget_ns;
     int32_t *status;
     int test_drop;                  // LDLT_TEST_DROP_UPDATE_COPIES: producer stops after one stage
-    TileMap tm;
-    int ntiles;
     int nst;
 };
 
@@ -239,8 +237,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) syrdk_tc_kernel(const TcArgs ar
     uint32_t *tmem_holder = (uint32_t *)(bars + 2 * NST + 5);
     volatile int *abort_flag = (volatile int *)(tmem_holder + 1);
 
+    // sizes of this panel's update (written by the kernels before this one);
+    // a CTA without a tile returns before it takes tensor memory
+    if (!step_live(args.ls, args.out)) return;
+    const int m_next = args.out->m_next, npiv = args.out->np;
+    if (m_next == 0 || npiv == 0) return;
+    const int kprime = args.la * ((npiv + 63) / 64 * 64);
+    TileMap tm;
+    tm.nI = (m_next + BM - 1) / BM;
+    tm.c = BM / args.bn;
+    tm.nfull = tm.c * (tm.nI - 1) * tm.nI / 2;
+    tm.nlast = (m_next + args.bn - 1) / args.bn;
+    const int ntiles = tm.nfull + tm.nlast;
+    if ((int)blockIdx.x >= ntiles) return;
+
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nk = args.kprime / KST;
+    const int nk = kprime / KST;
     const int np_ = args.nprime;
     const uint32_t stageB_bytes = (uint32_t)np_ * KST * 2;
 
@@ -272,11 +284,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) syrdk_tc_kernel(const TcArgs ar
         if (lane == 0) {
             uint32_t it = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < args.ntiles && ok; t += gridDim.x) {
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
                 int I, J;
-                tile_of(args.tm, t, I, J);
-                const __nv_bfloat16 *ablk = args.Aop + (int64_t)I * BM * args.kprime;
-                const __nv_bfloat16 *bblk = args.Bop + (int64_t)J * np_ * args.kprime;
+                tile_of(tm, t, I, J);
+                const __nv_bfloat16 *ablk = args.Aop + (int64_t)I * BM * kprime;
+                const __nv_bfloat16 *bblk = args.Bop + (int64_t)J * np_ * kprime;
                 for (int s = 0; s < nk; ++s, ++it) {
                     const uint32_t slot = it % NST, ph = (it / NST) & 1u;
                     if (args.test_drop && it >= 1) {
@@ -309,7 +321,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) syrdk_tc_kernel(const TcArgs ar
         const uint32_t idesc = make_idesc(BM, np_);
         uint32_t it = 0, tcount = 0;
         bool ok = true;
-        for (int t = blockIdx.x; t < args.ntiles && ok; t += gridDim.x, ++tcount) {
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tcount) {
             const uint32_t buf = tcount & 1u, tph = (tcount >> 1) & 1u;
             if (!mbar_wait(smem_u32(&bars[2 * NST + 2 + buf]), tph ^ 1u, args.budget_ns, abort_flag)) {
                 ok = false;
@@ -352,25 +364,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1) syrdk_tc_kernel(const TcArgs ar
         }
     } else {
         // ---------------- epilogue: two groups take alternate tiles ----------------
-        // Group g (warps 2+4g .. 5+4g) owns TMEM buffer g.  For its next tile it
+        // Group g (warps 2+8g .. 9+8g) owns TMEM buffer g.  For its next tile it
         // first gathers the old Schur values S[sigma i][sigma j] into shared
         // memory (this overlaps the MMAs of that tile), then drains the
         // accumulators: recombine the limbs, reduce once mod p, subtract, and
-        // store 16 consecutive columns of its row with vector stores.
-        const int g = (warp - 2) >> 2;       // group
-        const int wq = (warp - 2) & 3;       // warp within the group
+        // store its row's columns with vector stores.  The recombination is
+        // bound by instruction latency, so two warps share each TMEM lane
+        // quarter (warp w may read lanes 32 (w mod 4) .. +31), each taking
+        // half of the tile's columns.
+        const int g = (warp - 2) >> 3;       // group
+        const int wq = (warp - 2) & 7;       // warp within the group
         const int q = warp & 3;              // TMEM lane quarter this warp may access
+        const int hc = wq >> 2;              // column half of the tile this warp drains
         const int row = q * 32 + lane;       // tile row owned in the TMEM phase
         uint32_t *cg = cold + g * BM * CLD;
         const FieldP f = args.f;
         const int L = args.limbs;
-        const int mn = args.m_next;
+        const int mn = m_next;
         const uint64_t bias = args.bias;
         uint32_t tcount = g;
-        for (int t = blockIdx.x + g * gridDim.x; t < args.ntiles; t += 2 * gridDim.x, tcount += 2) {
+        for (int t = blockIdx.x + g * gridDim.x; t < ntiles; t += 2 * gridDim.x, tcount += 2) {
             int I, J;
-            tile_of(args.tm, t, I, J);
-            // -- gather the old values of this tile (rows wq*32 .. wq*32+31) --
+            tile_of(tm, t, I, J);
+            // -- gather the old values of this tile (rows wq*16 .. wq*16+15) --
             // Asynchronous 4-byte copies, all in flight at once: one memory
             // round trip per tile.  S is only read in this kernel (the new
             // values go to Snext), so the L1-allocating form sees no stale line.
@@ -378,14 +394,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) syrdk_tc_kernel(const TcArgs ar
                 const int j0 = J * BN + lane, j1 = j0 + 32;
                 const int sj0 = j0 < mn ? __ldg(args.sigma + j0) : 0;
                 const int sj1 = j1 < mn ? __ldg(args.sigma + j1) : 0;
-                const int ilane = I * BM + wq * 32 + lane;
+                const int ilane = I * BM + wq * 16 + (lane & 15);
                 const int si_lane = ilane < mn ? __ldg(args.sigma + ilane) : 0;
 #pragma unroll 8
-                for (int r = 0; r < 32; ++r) {
-                    const int i = I * BM + wq * 32 + r;
+                for (int r = 0; r < 16; ++r) {
+                    const int i = I * BM + wq * 16 + r;
                     const int si = __shfl_sync(0xffffffffu, si_lane, r);
                     const uint32_t *srow = args.S + (int64_t)si * args.ldS;
-                    const int rr = wq * 32 + r;
+                    const int rr = wq * 16 + r;
                     uint32_t *d0 = cg + rr * CLD + lane, *d1 = d0 + 32;
                     if (i < mn && j0 <= i && j0 < mn) cp_async4(d0, srow + sj0);
                     else *d0 = 0u;
@@ -395,7 +411,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) syrdk_tc_kernel(const TcArgs ar
                 asm volatile("cp.async.commit_group;\n" ::: "memory");
                 asm volatile("cp.async.wait_group 0;\n" ::: "memory");
             }
-            asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory");
+            asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "n"(GROUP_THREADS) : "memory");
             const uint32_t tph = (tcount >> 1) & 1u;
             if (!mbar_wait(smem_u32(&bars[2 * NST + g]), tph, args.budget_ns, abort_flag)) {
                 atomicExch(args.status, LDLT_ERR_TIMEOUT_CODE);
@@ -408,16 +424,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) syrdk_tc_kernel(const TcArgs ar
             uint32_t *drow = args.Snext + (int64_t)i * args.ldS;
             const uint32_t *crow = cg + row * CLD;
 #pragma unroll 1
-            for (int c0 = 0; c0 < BN; c0 += 16) {
-                uint32_t r[4][16];
-                tmem_ld16(tbase + (uint32_t)(0 * BN + c0), r[0]);
-                if (L > 1) tmem_ld16(tbase + (uint32_t)(1 * BN + c0), r[1]);
-                if (L > 2) tmem_ld16(tbase + (uint32_t)(2 * BN + c0), r[2]);
-                if (L > 3) tmem_ld16(tbase + (uint32_t)(3 * BN + c0), r[3]);
+            for (int c0 = hc * (BN / 2); c0 < (hc + 1) * (BN / 2); c0 += 8) {
+                uint32_t r[4][8];
+                tmem_ld8(tbase + (uint32_t)(0 * BN + c0), r[0]);
+                if (L > 1) tmem_ld8(tbase + (uint32_t)(1 * BN + c0), r[1]);
+                if (L > 2) tmem_ld8(tbase + (uint32_t)(2 * BN + c0), r[2]);
+                if (L > 3) tmem_ld8(tbase + (uint32_t)(3 * BN + c0), r[3]);
                 tmem_wait_ld();
-                uint32_t o[16];
+                uint32_t o[8];
 #pragma unroll
-                for (int e = 0; e < 16; ++e) {
+                for (int e = 0; e < 8; ++e) {
                     int64_t v = (int64_t)__float2int_rn(__uint_as_float(r[0][e]));
                     if (L > 1) v += (int64_t)__float2int_rn(__uint_as_float(r[1][e])) << 8;
                     if (L > 2) v += (int64_t)__float2int_rn(__uint_as_float(r[2][e])) << 16;
@@ -426,22 +442,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) syrdk_tc_kernel(const TcArgs ar
                 }
                 const int jb = J * BN + c0;
                 if (i < mn) {
-                    if (jb + 15 <= i && jb + 15 < mn) {
+                    if (jb + 7 <= i && jb + 7 < mn) {
                         uint4 *dst = (uint4 *)(drow + jb);
                         dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
                         dst[1] = make_uint4(o[4], o[5], o[6], o[7]);
-                        dst[2] = make_uint4(o[8], o[9], o[10], o[11]);
-                        dst[3] = make_uint4(o[12], o[13], o[14], o[15]);
                     } else {
 #pragma unroll
-                        for (int e = 0; e < 16; ++e)
+                        for (int e = 0; e < 8; ++e)
                             if (jb + e <= i && jb + e < mn) drow[jb + e] = o[e];
                     }
                 }
             }
             tc_fence_before();
             mbar_arrive(smem_u32(&bars[2 * NST + 2 + g]));
-            asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory");
+            asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "n"(GROUP_THREADS) : "memory");
         }
     }
 
@@ -484,11 +498,15 @@ __device__ __forceinline__ uint4 pack8(const int32_t *v)
 }
 
 struct SplitArgs {
-    const uint32_t *LpT;
+    const uint32_t *LpC;
     int64_t ldL;
     const int *sigma;
-    int m_next, np, rows, kpad, la, ash, lb, bn, nprime, kprime;  // A: la digits of base 2^ash
+    int la, ash, lb, bn, nprime;  // A: la digits of base 2^ash
+    const LoopState *ls;          // with out: m_next rows, np columns
     const PanelOut *out;
+    const uint32_t *S;            // np = 0: Snext = S[sigma, sigma]
+    int64_t ldS;
+    uint32_t *Snext;
     FieldP f;
     uint32_t wbase[4];  // beta^u mod p
     __nv_bfloat16 *Aop, *Bop;
@@ -497,23 +515,32 @@ struct SplitArgs {
 // One thread per (row i, group of 8 columns k..k+7).
 __global__ void split_tc_kernel(const SplitArgs a)
 {
+    if (!step_live(a.ls, a.out)) return;
+    const int m_next = a.out->m_next, np = a.out->np;
+    if (np == 0) {
+        compact_rows(a.S, a.ldS, a.sigma, m_next, a.Snext, blockIdx.y * gridDim.x + blockIdx.x,
+                     gridDim.x * gridDim.y);
+        return;
+    }
+    if (m_next == 0) return;
+    const int kpad = (np + 63) / 64 * 64, rows = (m_next + BM - 1) / BM * BM, kprime = a.la * kpad;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int k0 = blockIdx.y * 8;
-    if (i >= a.rows) return;
+    if (i >= rows || k0 >= kpad) return;
     const FieldP f = a.f;
     const int LA = a.la, LB = a.lb;
     uint32_t g[10];  // g[1 + e] = G[i][k0 + e], e in [-1, 8]
 #pragma unroll
     for (int e = 0; e < 10; ++e) {
         const int k = k0 - 1 + e;
-        g[e] = (i < a.m_next && k >= 0 && k < a.np) ? a.LpT[(int64_t)k * a.ldL + a.sigma[i]] : 0u;
+        g[e] = (i < m_next && k >= 0 && k < np) ? a.LpC[(int64_t)k * a.ldL + a.sigma[i]] : 0u;
     }
     int32_t gd_bal[8], gb[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
         const int k = k0 + e;
         uint32_t v = 0;
-        if (k < a.np) {
+        if (k < np) {
             const uint32_t ek = a.out->eval[k];
             if (ek != 0) v = fp_mul(ek, g[e + 2], f);
             else if (k > 0 && a.out->eval[k - 1] != 0)
@@ -532,12 +559,12 @@ __global__ void split_tc_kernel(const SplitArgs a)
         int32_t v8[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) v8[e] = dg[e][u];
-        const int kk = u * a.kpad + k0;
-        const int64_t off = (int64_t)I * BM * a.kprime + (int64_t)(kk / 8) * (BM * 8) + ri * 8;
+        const int kk = u * kpad + k0;
+        const int64_t off = (int64_t)I * BM * kprime + (int64_t)(kk / 8) * (BM * 8) + ri * 8;
         *(uint4 *)(a.Aop + off) = pack8(v8);
     }
     // B operand: base-256 digit v of b~_u = balanced(beta^u g mod p), rows v*bn + rj
-    if (i < ((a.rows + a.bn - 1) / a.bn) * a.bn) {
+    if (i < ((rows + a.bn - 1) / a.bn) * a.bn) {
         for (int u = 0; u < LA; ++u) {
             int32_t db[8][4];
 #pragma unroll
@@ -545,12 +572,12 @@ __global__ void split_tc_kernel(const SplitArgs a)
                 gb[e] = balanced(fp_mul(a.wbase[u], g[e + 1], f), f.p);
                 digits(gb[e], LB, 8, db[e]);
             }
-            const int kk = u * a.kpad + k0;
+            const int kk = u * kpad + k0;
             for (int v = 0; v < LB; ++v) {
                 int32_t v8[8];
 #pragma unroll
                 for (int e = 0; e < 8; ++e) v8[e] = db[e][v];
-                const int64_t off = (int64_t)J * a.nprime * a.kprime + (int64_t)(kk / 8) * (a.nprime * 8) +
+                const int64_t off = (int64_t)J * a.nprime * kprime + (int64_t)(kk / 8) * (a.nprime * 8) +
                                     (int64_t)(v * a.bn + rj) * 8;
                 *(uint4 *)(a.Bop + off) = pack8(v8);
             }
@@ -612,18 +639,18 @@ size_t tc_operand_bytes(int64_t n, int limbs)
     return (size_t)round_up(aBytes, 256) + (size_t)round_up(bBytes, 256);
 }
 
-cudaError_t launch_split_tc(const uint32_t *LpT, int64_t ldL, const int *sigma, int m_next, int np,
-                            const PanelOut *out, FieldP f, int limbs, int kpad, void *Aop, void *Bop,
-                            cudaStream_t st)
+cudaError_t launch_split_tc(const uint32_t *LpC, int64_t ldL, const int *sigma, int64_t n,
+                            const LoopState *ls, const PanelOut *out, FieldP f, int limbs, void *Aop,
+                            void *Bop, const uint32_t *S, int64_t ldS, uint32_t *Snext, cudaStream_t st)
 {
-    if (m_next == 0) return cudaSuccess;
+    if (n == 0) return cudaSuccess;
     SplitArgs a;
-    a.LpT = LpT; a.ldL = ldL; a.sigma = sigma; a.m_next = m_next; a.np = np;
-    a.rows = (int)round_up(m_next, BM);
+    a.LpC = LpC; a.ldL = ldL; a.sigma = sigma;
     int ash = 8;
-    a.kpad = kpad; a.lb = limbs; a.la = tc_limbs_a(f.p, &ash); a.ash = ash; a.bn = tc_bn(limbs);
-    a.nprime = limbs * a.bn; a.kprime = a.la * kpad;
-    a.out = out; a.f = f;
+    a.lb = limbs; a.la = tc_limbs_a(f.p, &ash); a.ash = ash; a.bn = tc_bn(limbs);
+    a.nprime = limbs * a.bn;
+    a.ls = ls; a.out = out; a.f = f;
+    a.S = S; a.ldS = ldS; a.Snext = Snext;
     uint64_t w = 1;
     for (int u = 0; u < 4; ++u) {
         a.wbase[u] = (uint32_t)(w % f.p);
@@ -631,36 +658,30 @@ cudaError_t launch_split_tc(const uint32_t *LpT, int64_t ldL, const int *sigma, 
     }
     a.Aop = (__nv_bfloat16 *)Aop;
     a.Bop = (__nv_bfloat16 *)Bop;
-    dim3 grid((a.rows + 127) / 128, kpad / 8);
+    // sized for the largest update (n rows, KP_MAX columns); surplus threads return
+    dim3 grid((unsigned)((round_up(n, BM) + 127) / 128), KP_MAX / 8);
     split_tc_kernel<<<grid, 128, 0, st>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_syrdk_tc(const uint32_t *S, int64_t ldS, const int *sigma, int m_next, const void *Aop,
-                            const void *Bop, int limbs, int kpad, FieldP f, uint32_t *Snext,
-                            int64_t budget_ns, int32_t *status, int num_sms, int test_drop,
-                            cudaStream_t st)
+cudaError_t launch_syrdk_tc(const uint32_t *S, int64_t ldS, const int *sigma, const LoopState *ls,
+                            const PanelOut *out, const void *Aop, const void *Bop, int limbs, FieldP f,
+                            uint32_t *Snext, int64_t budget_ns, int32_t *status, int num_sms,
+                            int test_drop, cudaStream_t st)
 {
-    if (m_next == 0) return cudaSuccess;
     TcArgs a;
-    a.S = S; a.ldS = ldS; a.sigma = sigma; a.m_next = m_next;
+    a.S = S; a.ldS = ldS; a.sigma = sigma; a.ls = ls; a.out = out;
     a.Aop = (const __nv_bfloat16 *)Aop; a.Bop = (const __nv_bfloat16 *)Bop;
     int ash = 8;
-    a.limbs = limbs; a.bn = tc_bn(limbs); a.nprime = limbs * a.bn; a.kprime = tc_limbs_a(f.p, &ash) * kpad;
+    a.limbs = limbs; a.bn = tc_bn(limbs); a.nprime = limbs * a.bn; a.la = tc_limbs_a(f.p, &ash);
     a.f = f;
     a.bias = ((((uint64_t)1 << 50) / f.p) + 1) * (uint64_t)f.p;
     a.Snext = Snext; a.budget_ns = budget_ns; a.status = status; a.test_drop = test_drop;
-    const int nI = (m_next + BM - 1) / BM;
-    a.tm.nI = nI;
-    a.tm.c = BM / a.bn;
-    a.tm.nfull = a.tm.c * (nI - 1) * nI / 2;
-    a.tm.nlast = (m_next + a.bn - 1) / a.bn;
-    a.ntiles = a.tm.nfull + a.tm.nlast;
     a.nst = NST;
     const size_t smem = 1024 + (size_t)NST * STAGE_BYTES + (size_t)2 * BM * CLD * 4 + 256;
     cudaError_t err = cudaFuncSetAttribute(syrdk_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    int grid = a.ntiles < num_sms ? a.ntiles : num_sms;
-    syrdk_tc_kernel<<<grid, TC_THREADS, smem, st>>>(a);
+    // persistent: one CTA per SM, the tile count is read on the device
+    syrdk_tc_kernel<<<num_sms, TC_THREADS, smem, st>>>(a);
     return cudaGetLastError();
 }

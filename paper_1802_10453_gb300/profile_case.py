@@ -1,14 +1,16 @@
 """One factorisation (or one batched call) for profiling under ncu.
 
-    python -m paper_1802_10453_gb300.profile_case N [p] [fp64]
-    python -m paper_1802_10453_gb300.profile_case WORKLOAD_NAME
+    python -m paper_1802_10453_gb300.profile_case N [p] [fp64] [host]
+    python -m paper_1802_10453_gb300.profile_case WORKLOAD_NAME [host]
     python -m paper_1802_10453_gb300.profile_case batch COUNT
     python -m paper_1802_10453_gb300.profile_case trss N [p]
 
 The first form draws A = T R T^T (n = N, rank N/2, a quarter of R's non-zeros
 in 2x2 pairs, p = 2^26 - 5 unless given) on the GPU; the second draws the named
 workload of inputs.WORKLOADS exactly as bench.py does; both factor it once
-through the C ABI.  The third draws the first COUNT matrices of the batch
+through the C ABI, as one CUDA graph, or with `host` from the profiling host
+loop (the same kernels launched one by one from the host, one readback per
+panel), which is what the ncu captures of single kernels use.  The third draws the first COUNT matrices of the batch
 workload (n in [32, 512], p = 65521) and factors them in one batched call.
 The fourth solves one TRSS (Algorithm 1) of order N (random upper triangular
 U with a non-zero diagonal, random symmetric C; p = 8388593 unless given).
@@ -48,6 +50,8 @@ def main(argv):
         torch.cuda.synchronize()
         print("trss n", n, "p", p, "status", int(st.item()))
         return 0 if int(st.item()) == 0 else 1
+    host = "host" in argv[2:]
+    argv = [a for a in argv if a != "host"]
     if arg in inputs.WORKLOADS:
         A, n, _, p, _ = inputs_gpu.workload_matrix(arg)
         path = lr.PATH_TC
@@ -57,8 +61,12 @@ def main(argv):
         path = lr.PATH_FP64 if (len(argv) > 3 and argv[3] == "fp64") else lr.PATH_TC
         r = n // 2
         A, _ = inputs_gpu.planted_matrix(n, r, r // 4, p, 12345)
+    if host:
+        lr.lib().ldlt_rpm_profile_enable(1)
     res = lr.factor(A, p, path=path)
     torch.cuda.synchronize()
+    if host:
+        lr.lib().ldlt_rpm_profile_enable(0)
     print("n", n, "p", p, "rank", int(res["rank"].item()), "status", int(res["status"].item()))
     return 0
 

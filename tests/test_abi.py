@@ -101,6 +101,7 @@ def test_noalloc_limits_on_host(libs):
     mb = int(re.search(r"#define LDLT_NOALLOC_BYTES\s+\(\(size_t\)(\d+) << 20\)", hdr).group(1))
     assert mb << 20 == libs.NOALLOC_BYTES
     assert int(re.search(r"#define LDLT_ERR_TOO_LARGE\s+(-\d+)", hdr).group(1)) == libs.LDLT_ERR_TOO_LARGE
+    assert int(re.search(r"#define LDLT_ERR_INTERNAL\s+(-\d+)", hdr).group(1)) == libs.LDLT_ERR_INTERNAL
     for p in (2, 3, 251, 65521, 8388593, 67108859, 2147483647):
         for path in (libs.PATH_FP64, libs.PATH_TC):
             try:
