@@ -536,6 +536,9 @@ def main():
     prof = (ctypes.c_double * 32)()
     L.ldlt_rpm_profile_read(prof)
     prof = [v / psteps for v in prof]
+    hbmp = (ctypes.c_double * 16)()
+    L.ldlt_rpm_profile_read_hbm(hbmp)
+    hbmp = [v / psteps for v in hbmp]
     if int(pres["status"].item()) != 0 or int(pres["rank"].item()) != rank_found:
         raise SystemExit("profiled pass disagrees with the timed one")
     from paper_1802_10453_gb300.replicas import max_over_ranks, whole_job_rate
@@ -561,6 +564,7 @@ def main():
     peak = pk.get("bf16_tflops", 1900.0)
     peak_sus = pk.get("bf16_tflops_sustained", 1700.0)
     traffic = profile_traffic(os.path.join(ROOT, "paper_1802_10453_gb300", "csrc", "syrdk_tc.cu"))
+    syrdk_alg_bytes = hbmp[12] / hbmp[13] if hbmp[13] else None  # per launch
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": (achieved / peak) if achieved else None,
                 "traffic": (traffic / launches if (traffic is not None and launches) else None),
@@ -572,7 +576,25 @@ def main():
                 "avg_launch_ms": syrdk_ms / launches if launches else None,
                 "launches_per_step": launches,
                 "alg_flops_per_step": flops_issued_alg,
+                "alg_bytes_per_launch": syrdk_alg_bytes,
+                "traffic_over_alg_bytes": ((traffic / launches) / syrdk_alg_bytes
+                                           if (traffic is not None and launches and syrdk_alg_bytes) else None),
                 "timing": "CUDA events around each launch in a profiled pass of %d step(s)" % psteps}
+
+    # the HBM-streaming kernels: algorithmic bytes (counted by the library from
+    # the launch sizes) over their CUDA-event time, against the measured copy peak
+    hbm_peak = pk.get("hbm_gbs", 6800.0)
+    hbm_kernels = {}
+    for i, name in enumerate(["ingest_kernel", "finalize_kernel", "lw_scatter_kernel", "split_tc_kernel"]):
+        ms_k, nl, alg = hbmp[i], hbmp[4 + i], hbmp[8 + i]
+        if ms_k > 0 and nl > 0:
+            gbs = alg / (ms_k * 1e-3) / 1e9
+            hbm_kernels[name] = {"launches": nl, "ms": ms_k, "alg_bytes": alg, "achieved_gbs": gbs,
+                                 "frac": gbs / hbm_peak}
+    hbm_kernels["peak_gbs"] = hbm_peak
+    hbm_kernels["peak_source"] = ("measured copy (MEASURED_PEAKS.json)" if pk_kind == "measured"
+                                  else "fallback 6.8 TB/s")
+    hbm_kernels["timing"] = "CUDA events around each launch in the profiled pass (per step)"
 
     phases = {"pivot_chain_ms": prof[0], "operand_prep_ms": prof[1],
               "syrdk_ms": syrdk_ms, "panels": prof[6], "far_scans": prof[7],
@@ -771,6 +793,7 @@ def main():
             "parity": {"rpm_equals_planted": parity},
             "phases": phases,
             "roofline": roofline,
+            "hbm_kernels": hbm_kernels,
             "clocks": clocks,
             "e2e": e2e,
             "gpu_launches": graph_launches(prof[6]) * args.steps,

@@ -419,6 +419,29 @@ void ldlt_rpm_profile_enable(int on);
 void ldlt_rpm_profile_reset(void);
 int ldlt_rpm_profile_read(double out[32]);
 
+/*
+ * ldlt_rpm_profile_read_hbm -- the HBM-streaming kernels, from the same
+ * profiled calls (CUDA events around each launch; the algorithmic bytes are
+ * counted on the host from the sizes each launch was given):
+ *   out[0..3]   ms in ingest, finalize, L scatter, operand split
+ *   out[4..7]   their launches
+ *   out[8..11]  their algorithmic bytes: ingest 8 n(n+1)/2 (lower triangle of
+ *               A read, of S written); finalize 8 n(n+1)/2 (L rows read, an
+ *               upper bound since non-pivot rows read fewer columns, A's lower
+ *               triangle written); L scatter 8 np m per panel (np columns of
+ *               m rows read, and written by row); split 4 np m' (the columns
+ *               of the m' remaining rows) plus the operands written: tensor
+ *               form 2 L_A kpad R (1 + L_B) with R = m' rounded up to 128,
+ *               FP64 form 16 kpad ldS
+ *   out[12]     algorithmic bytes of the level-3 updates: per launch the old
+ *               lower triangle of the m' remaining rows read and the new one
+ *               written, 8 m'(m'+1)/2, plus the operands once (as above)
+ *   out[13]     level-3 update launches
+ *   out[14..15] reserved (0)
+ * Returns LDLT_OK, or LDLT_ERR_ARG for a NULL pointer.
+ */
+int ldlt_rpm_profile_read_hbm(double out[16]);
+
 #ifdef __cplusplus
 }
 #endif

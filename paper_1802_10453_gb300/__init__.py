@@ -1,8 +1,10 @@
 """GB300 (sm_103a) rank-profile-revealing symmetric factorisation mod p.
 
-Thin Python binding of the C ABI in ``include/ldlt_rpm.h`` (argument
-marshalling only; every step runs in the CUDA library).  PyTorch supplies
-device memory and streams.
+Thin Python binding of the C ABI in ``include/ldlt_rpm.h``: argument
+marshalling, with every step of the factorisation in the CUDA library
+(factor_recursive also derives the recursive algorithms' pivot order from
+R_A on the host between two library calls).  PyTorch supplies device memory
+and streams.
 
     import torch, paper_1802_10453_gb300 as lr
     res = lr.factor(A_cuda_uint32_view, p, path=lr.PATH_TC)

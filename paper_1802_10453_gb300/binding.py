@@ -1,8 +1,13 @@
 """ctypes binding of libldlt_rpm.so (C ABI of include/ldlt_rpm.h).
 
-Marshalling only: tensors are passed as raw device pointers; every computation
-runs in the CUDA library.  The library is loaded on first use and a missing
-library is an error -- there is no fallback path.
+Tensors are passed as raw device pointers and every step of the
+factorisation runs in the CUDA library; the wrappers marshal arguments and
+check status words.  One wrapper does host work beyond that:
+factor_recursive() derives the pivot order of the recursive Algorithms 2/3
+from R_A on the host (recursive_order.py, a permutation computed from the
+rank profile matrix, not arithmetic of the factorisation) between two
+library calls.  The library is loaded on first use and a missing library is
+an error -- there is no fallback path.
 """
 from __future__ import annotations
 

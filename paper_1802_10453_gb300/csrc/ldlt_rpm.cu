@@ -35,7 +35,11 @@ int g_test_drop = 0;  // failure-detection tests: LDLT_TEST_DROP_*
 struct Prof {
     bool on = false;
     double acc[32] = {};
-    cudaEvent_t ev[4] = {};  // panel start, after the panel, after the operand split, step end
+    double hbm[16] = {};     // see ldlt_rpm_profile_read_hbm
+    // panel start, after the panel, after the L scatter, after the operand
+    // split, after the update; ingest and finalize start / end
+    cudaEvent_t ev[5] = {};
+    cudaEvent_t evh[4] = {};
     bool ready = false;
 };
 Prof g_prof;
@@ -44,6 +48,7 @@ void prof_init()
 {
     if (!g_prof.ready) {
         for (auto &e : g_prof.ev) cudaEventCreate(&e);
+        for (auto &e : g_prof.evh) cudaEventCreate(&e);
         g_prof.ready = true;
     }
 }
@@ -53,13 +58,13 @@ void prof_init()
 void prof_collect()
 {
     cudaEvent_t *ev = g_prof.ev;
-    float t01 = 0, t12 = 0, t23 = 0;
-    cudaEventElapsedTime(&t01, ev[0], ev[1]);
-    cudaEventElapsedTime(&t12, ev[1], ev[2]);
-    cudaEventElapsedTime(&t23, ev[2], ev[3]);
-    g_prof.acc[0] += t01;
-    g_prof.acc[1] += t12;
-    g_prof.acc[2] += t23;
+    float t[4] = {0, 0, 0, 0};
+    for (int i = 0; i < 4; ++i) cudaEventElapsedTime(&t[i], ev[i], ev[i + 1]);
+    g_prof.acc[0] += t[0];
+    g_prof.acc[1] += t[1] + t[2];
+    g_prof.acc[2] += t[3];
+    g_prof.hbm[2] += t[1];
+    g_prof.hbm[3] += t[2];
 }
 
 uint64_t mulmod64(uint64_t a, uint64_t b, uint64_t m) { return (uint64_t)((unsigned __int128)a * b % m); }
@@ -191,12 +196,20 @@ extern "C" void ldlt_rpm_profile_enable(int on)
 extern "C" void ldlt_rpm_profile_reset(void)
 {
     for (double &a : g_prof.acc) a = 0.0;
+    for (double &a : g_prof.hbm) a = 0.0;
 }
 
 extern "C" int ldlt_rpm_profile_read(double out[32])
 {
     if (!out) return LDLT_ERR_ARG;
     for (int i = 0; i < 32; ++i) out[i] = g_prof.acc[i];
+    return LDLT_OK;
+}
+
+extern "C" int ldlt_rpm_profile_read_hbm(double out[16])
+{
+    if (!out) return LDLT_ERR_ARG;
+    for (int i = 0; i < 16; ++i) out[i] = g_prof.hbm[i];
     return LDLT_OK;
 }
 
@@ -311,21 +324,24 @@ void plan_make(Plan &c, int64_t n, uint32_t p, int path, uint32_t *A, int64_t ld
     }
 }
 
-// status = 0, S = lower(A) mod p (or P^T A P), loop state at order n
-cudaError_t enqueue_start(const Plan &c, cudaStream_t st)
+// status = 0, S = lower(A) mod p (or P^T A P), loop state at order n.
+// ev (profiling) brackets the ingest.
+cudaError_t enqueue_start(const Plan &c, cudaStream_t st, cudaEvent_t *ev = nullptr)
 {
     cudaError_t err = cudaMemsetAsync(c.status, 0, sizeof(int32_t), st);
     if (err != cudaSuccess) return err;
+    if (ev && (err = cudaEventRecord(ev[0], st)) != cudaSuccess) return err;
     err = c.gperm ? launch_ingest_perm(c.A, c.lda, c.n, c.gperm, c.Sbuf[0], c.ldS, c.idxb[0], c.f, c.gbad, st)
                   : launch_ingest(c.A, c.lda, c.n, c.Sbuf[0], c.ldS, c.idxb[0], c.f, st);
     if (err != cudaSuccess) return err;
+    if (ev && (err = cudaEventRecord(ev[1], st)) != cudaSuccess) return err;
     return launch_loop_step(c.ls, c.out, 1, c.n, c.status, c.LpT, c.ldS, c.consumed, c.sync, 0, 0, c.nsm, st);
 }
 
 // One panel step on half h: pivot chain (which also appends to the pivot and
 // zero-row lists), L columns, operand split, level-3 update (the split does
 // the compaction of a panel without pivots), loop advance.  ev (profiling):
-// panel start, panel end, split end, update end.
+// panel start, panel end, scatter end, split end, update end.
 cudaError_t enqueue_step(const Plan &c, int h, cudaGraphConditionalHandle cond, int set_cond, cudaEvent_t *ev,
                          cudaStream_t st)
 {
@@ -338,38 +354,51 @@ cudaError_t enqueue_step(const Plan &c, int h, cudaGraphConditionalHandle cond, 
     EQ(launch_panel(c.pp[h], c.pgrid, st));
     if (ev) EQ(cudaEventRecord(ev[1], st));
     EQ(launch_lw_scatter(c.LpC, c.ldS, c.n, c.ls, c.out, c.idxb[h], c.Lw, c.ldS, st));
+    if (ev) EQ(cudaEventRecord(ev[2], st));
     if (c.path == LDLT_PATH_FP64) {
         double *GDT = (double *)c.opA;
         double *GT = GDT + (size_t)KP_MAX * c.ldS;
         EQ(launch_split_fp64(c.LpC, c.ldS, c.sigma, c.n, c.ls, c.out, c.f, GDT, GT, c.ldS, c.Sbuf[h], c.ldS,
                              c.Sbuf[h ^ 1], st));
-        if (ev) EQ(cudaEventRecord(ev[2], st));
+        if (ev) EQ(cudaEventRecord(ev[3], st));
         EQ(launch_syrdk_fp64(c.Sbuf[h], c.ldS, c.sigma, c.n, c.ls, c.out, GDT, GT, c.ldS, c.f, c.Sbuf[h ^ 1], st));
     } else {
         EQ(launch_split_tc(c.LpC, c.ldS, c.sigma, c.n, c.ls, c.out, c.f, c.limbs, c.opA, c.opB, c.Sbuf[h], c.ldS,
                            c.Sbuf[h ^ 1], st));
-        if (ev) EQ(cudaEventRecord(ev[2], st));
+        if (ev) EQ(cudaEventRecord(ev[3], st));
         EQ(launch_syrdk_tc(c.Sbuf[h], c.ldS, c.sigma, c.ls, c.out, c.opA, c.opB, c.limbs, c.f, c.Sbuf[h ^ 1],
                            g_budget_ns, c.status, c.nsm, g_test_drop == LDLT_TEST_DROP_UPDATE_COPIES, st));
     }
-    if (ev) EQ(cudaEventRecord(ev[3], st));
+    if (ev) EQ(cudaEventRecord(ev[4], st));
     EQ(launch_loop_step(c.ls, c.out, 0, c.n, c.status, c.LpT, c.ldS, c.consumed, c.sync, cond, set_cond, c.nsm,
                         st));
     return cudaSuccess;
 #undef EQ
 }
 
-cudaError_t enqueue_finish(const Plan &c, cudaStream_t st)
+cudaError_t enqueue_finish(const Plan &c, cudaStream_t st, cudaEvent_t *ev = nullptr)
 {
-    return launch_finalize(c.n, c.Lw, c.ldS, c.piv_all, c.d_all, c.e_all, c.zero_all, c.zero_cols, c.ls, c.A,
-                           c.lda, c.perm, c.e, c.rank, st);
+    cudaError_t err;
+    if (ev && (err = cudaEventRecord(ev[0], st)) != cudaSuccess) return err;
+    err = launch_finalize(c.n, c.Lw, c.ldS, c.piv_all, c.d_all, c.e_all, c.zero_all, c.zero_cols, c.ls, c.A,
+                          c.lda, c.perm, c.e, c.rank, st);
+    if (err != cudaSuccess) return err;
+    if (ev && (err = cudaEventRecord(ev[1], st)) != cudaSuccess) return err;
+    return cudaSuccess;
 }
 
 // Profiling: the same kernels from a host loop, one readback per panel.
 int run_profiled(const Plan &c, cudaStream_t st)
 {
-    CK(enqueue_start(c, st));
+    double *hb = g_prof.hbm;
+    const double tri = (double)c.n * (double)(c.n + 1) * 0.5;
+    CK(enqueue_start(c, st, g_prof.evh));
     g_prof.acc[5] += 2;  // ingest, loop start
+    hb[4] += 1;
+    hb[8] += 8.0 * tri;  // lower triangle of A read, of S written
+    int m = (int)c.n;
+    int lb = 0, la = 0, ash = 8;
+    if (c.path == LDLT_PATH_TC) { lb = c.limbs; la = tc_limbs_a(c.p, &ash); }
     for (int ipanel = 0;; ++ipanel) {
         CK(enqueue_step(c, ipanel & 1, 0, 0, g_prof.ev, st));
         struct { int h[8]; long long cyc[8]; long long dbg[16]; } rb;
@@ -390,10 +419,34 @@ int run_profiled(const Plan &c, cudaStream_t st)
             g_prof.acc[3] += (double)m_next * (double)(m_next + 1) * 0.5 * (double)np;
             g_prof.acc[4] += 1;
         }
+        if (!hdr[4] && np > 0) {
+            hb[6] += 1;
+            hb[10] += 8.0 * (double)np * (double)m;  // np L columns of m rows read, written by row
+            if (m_next > 0) {
+                const double kpad = (double)round_up(np, 64), rows = (double)round_up(m_next, 128);
+                hb[7] += 1;
+                hb[11] += 4.0 * (double)np * (double)m_next;  // the columns of the remaining rows
+                const double ops = c.path == LDLT_PATH_TC ? 2.0 * rows * la * kpad * (1.0 + lb)  // A' and B'
+                                                          : 2.0 * 8.0 * kpad * (double)c.ldS;     // GD^T and G^T
+                hb[11] += ops;
+                // the update: the old lower triangle read and the new one written, the operands read once
+                hb[12] += 8.0 * (double)m_next * (double)(m_next + 1) * 0.5 + ops;
+                hb[13] += 1;
+            }
+        }
+        m = m_next;
         if (lh.done) break;
     }
-    CK(enqueue_finish(c, st));
+    CK(enqueue_finish(c, st, g_prof.evh + 2));
     g_prof.acc[5] += 1;
+    CK(cudaStreamSynchronize(st));
+    float ti = 0, tf = 0;
+    cudaEventElapsedTime(&ti, g_prof.evh[0], g_prof.evh[1]);
+    cudaEventElapsedTime(&tf, g_prof.evh[2], g_prof.evh[3]);
+    hb[0] += ti;
+    hb[1] += tf;
+    hb[5] += 1;
+    hb[9] += 8.0 * tri;  // L rows read (an upper bound: zero rows read fewer), A's lower triangle written
     return LDLT_OK;
 }
 
