@@ -1,10 +1,14 @@
 """In-tree build of the CUDA libraries for sm_103a (nvcc, no cmake).
 
-    python -m paper_1802_10453_gb300.build
+    python -m paper_1802_10453_gb300.build [--force] [--chain-profile]
 
 produces ``libldlt_rpm.so`` (the factorisation, C ABI of include/ldlt_rpm.h)
 and ``libldlt_gen.so`` (the GPU input generator) next to this file.  Sources
 compile in parallel; a library is rebuilt only when a source is newer.
+--chain-profile rebuilds everything with LDLT_CHAIN_PROFILE defined: the
+pivot chain then also records SM-cycle counters per leader phase and per
+barrier (ldlt_rpm_profile_read out[8..15], out[26..31]); a later plain build
+must be forced to drop them.
 """
 from __future__ import annotations
 
@@ -33,7 +37,9 @@ def _newest(paths):
     return max(os.path.getmtime(p) for p in paths)
 
 
-def build(force: bool = False, verbose: bool = False) -> dict:
+def build(force: bool = False, verbose: bool = False, chain_profile: bool = False) -> dict:
+    flags = FLAGS + (["-DLDLT_CHAIN_PROFILE"] if chain_profile else [])
+    force = force or chain_profile
     os.makedirs(BUILD, exist_ok=True)
     hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", "ldlt_rpm.h")]
     out = {}
@@ -48,7 +54,7 @@ def build(force: bool = False, verbose: bool = False) -> dict:
             o = os.path.join(BUILD, os.path.basename(s) + ".o")
             objs.append(o)
             if stale and (force or not os.path.exists(o) or os.path.getmtime(o) < _newest([s] + hdrs)):
-                cmd = [NVCC] + ARCH + FLAGS + ["-c", s, "-o", o]
+                cmd = [NVCC] + ARCH + flags + ["-c", s, "-o", o]
                 jobs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
         plan.append((lib, target, objs, stale))
         out[lib] = target
@@ -69,4 +75,4 @@ def build(force: bool = False, verbose: bool = False) -> dict:
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, chain_profile="--chain-profile" in sys.argv))

@@ -68,7 +68,9 @@ namespace {
 constexpr int NCW = 16;                       // compute warps
 constexpr int NCT = NCW * 32;                 // compute threads (2 per row)
 constexpr int SROWS = 256;                    // rows held in shared memory per CTA
-constexpr int SSTRIDE = SROWS + 16;           // padded k-row stride (words)
+constexpr int RS = KP_MAX + 8;                // U~ row stride (words): 8 mod 32, so the 16-byte
+                                              // loads of 4 consecutive rows x 2 k-groups of a
+                                              // quarter warp hit distinct banks
 constexpr int NSLOT = 8;                      // event ring slots
 constexpr int BLOCK = PANEL_THREADS_V2;
 
@@ -129,7 +131,7 @@ static_assert(KP_MAX <= CTL, "the control thread computes no z entry");
 constexpr int SRING = 128;                    // posted scan results
 
 struct Shared {
-    uint32_t U[KP_MAX * SSTRIDE];      // U~ columns of this CTA's rows, k-major
+    uint32_t U[SROWS * RS];            // U~ of this CTA's rows, row-major
     uint32_t ring[NSLOT][EV_WORDS];    // event payloads
     uint32_t scol[NSLOT][2][SROWS];    // helpers: S(t, a) and S(t, b) of each ring event
     uint4 sgrp[2][SROWS];              // helpers: S[t][4g .. 4g+3] for two column groups
@@ -218,9 +220,12 @@ __device__ __forceinline__ uint32_t zval(int k, const uint32_t *u, int stride, c
     return fp_mul(t, sh.bw[kb], f);
 }
 
-// c~_z[t] = W S(t, a) - sum_{k < np} U~[t][k] z[k], two threads per row (half
-// = tid & 1 takes every other k).  All 32 lanes must call it (pair shuffle);
-// invalid rows compute nothing and return 0.
+// c~_z[t] = W S(t, a) - sum_{k < np} U~[t][k] z[k], two threads per row.  In
+// shared memory (row-major) half = tid & 1 takes the k-groups 8j + 4 half ..
+// +3 with 16-byte loads of the row and of z (z is 16-byte aligned and zero
+// from np to the next multiple of 8); rows kept in
+// global memory (k-major) take every other k.  All 32 lanes must call it
+// (pair shuffle); invalid rows compute nothing and return 0.
 template <bool BIG>
 __device__ __forceinline__ uint32_t schur2(const PanelParams &P, const uint32_t *sU, int lrow, int grow,
                                           uint32_t sval, uint32_t W, const uint32_t *z, int np, int half,
@@ -229,9 +234,17 @@ __device__ __forceinline__ uint32_t schur2(const PanelParams &P, const uint32_t 
     uint64_t acc = 0;
     if (valid) {
         if (in_smem) {
-            const uint32_t *col = sU + lrow;
-#pragma unroll 4
-            for (int k = half; k < np; k += 2) mac<BIG>(acc, col[k * SSTRIDE], z[k], P.f);
+            const uint4 *row = reinterpret_cast<const uint4 *>(sU + lrow * RS + 4 * half);
+            const uint4 *zv = reinterpret_cast<const uint4 *>(z + 4 * half);
+            const int ng = (np + 7) >> 3;
+#pragma unroll 2
+            for (int j = 0; j < ng; ++j) {
+                const uint4 u = row[2 * j], zz = zv[2 * j];
+                mac<BIG>(acc, u.x, zz.x, P.f);
+                mac<BIG>(acc, u.y, zz.y, P.f);
+                mac<BIG>(acc, u.z, zz.z, P.f);
+                mac<BIG>(acc, u.w, zz.w, P.f);
+            }
         } else {
             const uint32_t *col = P.LpT + grow;
             for (int k = half; k < np; k += 2) mac<BIG>(acc, col[(int64_t)k * P.ldL], z[k], P.f);
@@ -272,6 +285,10 @@ __device__ void helper_cta(const PanelParams &P, Shared &sh, int lo, int hi)
     const int warp = tid >> 5, lane = tid & 31;
     const int nrows = hi > lo ? hi - lo : 0;
     if (tid == 0) { sh.ev_ready = 0; sh.ev_done = 0; sh.quit = 0; sh.ev_fetched = 0; }
+    {
+        const int nz = (nrows < SROWS ? nrows : SROWS) * RS / 4;
+        for (int i = tid; i < nz; i += blockDim.x) reinterpret_cast<uint4 *>(sh.U)[i] = make_uint4(0, 0, 0, 0);
+    }
     __syncthreads();
 
     if (warp == NCW) {
@@ -444,7 +461,7 @@ __device__ void helper_cta(const PanelParams &P, Shared &sh, int lo, int hi)
             cbar();
             for (int lr = tid; lr < nrows; lr += NCT) {
                 const int t = lo + lr;
-                if (lr < SROWS) finish_row(P, sh.U + lr, SSTRIDE, P.LpC + t, np, sh.kind, cA, cB);
+                if (lr < SROWS) finish_row(P, sh.U + lr * RS, 1, P.LpC + t, np, sh.kind, cA, cB);
                 else finish_row(P, P.LpT + t, (int)P.ldL, P.LpC + t, np, sh.kind, cA, cB);
             }
             hflush();
@@ -460,7 +477,7 @@ __device__ void helper_cta(const PanelParams &P, Shared &sh, int lo, int hi)
             if (kind == EV_PIVOT1) {
                 const uint32_t c = schur2<BIG>(P, sh.U, lr, t, sa, W, za, np, half, valid, sm);
                 if (valid && half == 0) {
-                    if (sm) sh.U[np * SSTRIDE + lr] = c;
+                    if (sm) sh.U[lr * RS + np] = c;
                     P.LpT[(int64_t)np * P.ldL + t] = c;
                 }
             } else if (kind == EV_PIVOT2) {
@@ -468,7 +485,7 @@ __device__ void helper_cta(const PanelParams &P, Shared &sh, int lo, int hi)
                 const uint32_t ca = schur2<BIG>(P, sh.U, lr, t, sa, W, za, np, half, valid, sm);
                 const uint32_t cb = schur2<BIG>(P, sh.U, lr, t, sb, W, zb, np, half, valid, sm);
                 if (valid && half == 0) {
-                    if (sm) { sh.U[np * SSTRIDE + lr] = ca; sh.U[(np + 1) * SSTRIDE + lr] = cb; }
+                    if (sm) { sh.U[lr * RS + np] = ca; sh.U[lr * RS + np + 1] = cb; }
                     P.LpT[(int64_t)np * P.ldL + t] = ca;
                     P.LpT[(int64_t)(np + 1) * P.ldL + t] = cb;
                 }
@@ -490,7 +507,7 @@ __device__ void helper_cta(const PanelParams &P, Shared &sh, int lo, int hi)
                 uint32_t *dst = P.partner_lp +
                                 ((int64_t)(sid % SCAN_RING) * MAX_PANEL_GRID + blockIdx.x) * PSTR;
                 for (int k = tid; k < np; k += NCT)
-                    dst[k] = lr < SROWS ? sh.U[k * SSTRIDE + lr] : P.LpT[(int64_t)k * P.ldL + mn];
+                    dst[k] = lr < SROWS ? sh.U[lr * RS + k] : P.LpT[(int64_t)k * P.ldL + mn];
                 __threadfence();
                 cbar();
                 if (tid == 0) {
@@ -523,6 +540,7 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, const int m, const 
     const bool helpers = nh > 0;
     for (int t = tid; t < W0; t += blockDim.x) sh.wstate[t] = 0;
     for (int i = tid; i < SRING; i += blockDim.x) sh.res_ok[i] = 0;
+    for (int i = tid; i < SROWS * RS / 4; i += blockDim.x) reinterpret_cast<uint4 *>(sh.U)[i] = make_uint4(0, 0, 0, 0);
     if (tid == 0) {
         sh.np = 0; sh.ia = 0; sh.nzero = 0; sh.nscan = 0; sh.abort = 0; sh.nblk = 0;
         sh.ev_ready = 0; sh.ev_done = 0; sh.quit = 0; sh.W = 1u;
@@ -560,7 +578,8 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, const int m, const 
                 const int words = (kind == EV_END) ? 3 * KP_MAX : (kind == EV_PIVOT2 ? 2 * KP_MAX : KP_MAX);
                 for (int k = lane; k < words; k += 32) {
                     const int kk = k % KP_MAX;
-                    if (kind == EV_END || kk < np) rec[8 + k] = sh.ring[s][k];
+                    // z vectors with their zero padding to a multiple of 8
+                    if (kind == EV_END || kk < ((np + 7) & ~7)) rec[8 + k] = sh.ring[s][k];
                 }
                 if (lane < 8) rec[lane] = reinterpret_cast<const uint32_t *>(&sh.ev[s])[lane];
                 if (kind == EV_SCAN) {
@@ -754,7 +773,7 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, const int m, const 
         }
         for (int q = tid; q < (np - npk) * w; q += NCT) {
             const int j = npk + q / w, t = q % w;
-            sh.U[j * SSTRIDE + t] = 0;
+            sh.U[t * RS + j] = 0;
             P.LpT[(int64_t)j * P.ldL + t] = 0;
         }
         np = npk;
@@ -798,9 +817,12 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, const int m, const 
         const int slot = ev_next % NSLOT;
         uint32_t *za = sh.ring[slot];
         uint32_t *zb = sh.ring[slot] + KP_MAX;
-        if (tid < np) {
+        // z beyond np up to the next multiple of 8 is zero: the dot products read
+        // whole 8-column groups and a CTA's U~ may hold stale columns there
+        // (written before a rollback)
+        if (tid < ((np + 7) & ~7)) {
             ring_ready(ev_next);
-            za[tid] = zval(tid, sh.U + a, SSTRIDE, sh, f);
+            za[tid] = tid < np ? zval(tid, sh.U + a * RS, 1, sh, f) : 0u;
         }
         if (warp == NCW - 1) {
             if (lane == 0) sh.dbg[0] += 1;
@@ -861,7 +883,7 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, const int m, const 
         if (caa != 0) {
             // ---- 1x1 pivot: U~[:, np] = c~_a, delta = W c~_a[a] ----
             if (myrow && half == 0) {
-                sh.U[np * SSTRIDE + lr] = ca_t;
+                sh.U[lr * RS + np] = ca_t;
                 P.LpT[(int64_t)np * P.ldL + lr] = ca_t;
             }
             const uint32_t delta = fp_mul(W, caa, f);
@@ -953,9 +975,9 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, const int m, const 
             s_ab = s_at(P.S, P.ldS, a, b);
             s_bb = s_at(P.S, P.ldS, b, b);
         }
-        if (!far && tid < np) sh.ub[tid] = sh.U[tid * SSTRIDE + b];
+        if (!far && tid < np) sh.ub[tid] = sh.U[b * RS + tid];
         cbar();
-        if (tid < np) zb[tid] = zval(tid, sh.ub, 1, sh, f);
+        if (tid < ((np + 7) & ~7)) zb[tid] = tid < np ? zval(tid, sh.ub, 1, sh, f) : 0u;
         cbar();
         // x~ = W S(a,b) - U~[b] . z_a ;  y~ = W S(b,b) - U~[b] . z_b   (warp 0)
         if (warp == 0) {
@@ -980,8 +1002,8 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, const int m, const 
         cbar();
         const uint32_t x = sh.xy[0], y = sh.xy[1];
         if (myrow && half == 0) {
-            sh.U[np * SSTRIDE + lr] = ca_t;  // c~_a[a] = 0 here
-            sh.U[(np + 1) * SSTRIDE + lr] = cb_t;
+            sh.U[lr * RS + np] = ca_t;  // c~_a[a] = 0 here
+            sh.U[lr * RS + np + 1] = cb_t;
             P.LpT[(int64_t)np * P.ldL + lr] = ca_t;
             P.LpT[(int64_t)(np + 1) * P.ldL + lr] = cb_t;
         }
@@ -1084,7 +1106,7 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, const int m, const 
             }
         }
         // rewrite the window rows as true L columns
-        for (int t = tid; t < w; t += NCT) finish_row(P, sh.U + t, SSTRIDE, P.LpC + t, np, sh.kind, sh.cA, sh.cB);
+        for (int t = tid; t < w; t += NCT) finish_row(P, sh.U + t * RS, 1, P.LpC + t, np, sh.kind, sh.cA, sh.cB);
     }
     cbar();
     if (tid == 0) { __threadfence_block(); sh.quit = 1; }
