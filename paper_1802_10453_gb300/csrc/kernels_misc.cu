@@ -148,30 +148,16 @@ __global__ void __launch_bounds__(256) finalize_kernel(int64_t n, const uint32_t
 
 // Start (init) or advance the panel loop; see launch_loop_step.  Block 0
 // updates the state; every block clears its share of the next panel's
-// scratch, sized from the panel record alone (never from the state block 0
-// is writing).
+// partner flags, sized from the panel record alone (never from the state
+// block 0 is writing).
 __global__ void __launch_bounds__(256) loop_step_kernel(LoopState *ls, const PanelOut *out, int init, int64_t n,
-                                                        int32_t *status, uint32_t *LpT, int64_t ldL,
-                                                        uint8_t *consumed, PanelSync *sync,
+                                                        int32_t *status, uint8_t *consumed, PanelSync *sync,
                                                         cudaGraphConditionalHandle cond, int set_cond)
 {
     const int mclr = init ? (int)n : (out->abort ? 0 : out->m_next);
     const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (mclr > 0) {
-        if ((ldL & 3) == 0) {
-            // rows of LpT start on 16-byte boundaries: clear [0, round_up(m, 4)) of each
-            const int64_t q4 = ((int64_t)mclr + 3) >> 2, total = q4 * KP_MAX;
-            for (int64_t q = tid; q < total; q += nthr) {
-                const int64_t k = q / q4, c = q - k * q4;
-                reinterpret_cast<uint4 *>(LpT + k * ldL)[c] = make_uint4(0, 0, 0, 0);
-            }
-        } else {
-            const int64_t total = (int64_t)mclr * KP_MAX;
-            for (int64_t q = tid; q < total; q += nthr) LpT[(q / mclr) * ldL + q % mclr] = 0u;
-        }
-        for (int64_t t = tid; t < mclr; t += nthr) consumed[t] = 0;
-    }
+    for (int64_t t = tid; t < mclr; t += nthr) consumed[t] = 0;
     if (blockIdx.x != 0) return;
     if (threadIdx.x == 0) {
         *sync = PanelSync{0, 0, 0, 0};
@@ -260,15 +246,13 @@ cudaError_t launch_lw_scatter(const uint32_t *LpC, int64_t ldL, int64_t n, const
 }
 
 cudaError_t launch_loop_step(LoopState *ls, const PanelOut *out, int init, int64_t n, int32_t *status,
-                             uint32_t *LpT, int64_t ldL, uint8_t *consumed, PanelSync *sync,
-                             cudaGraphConditionalHandle cond, int set_cond, int num_sms, cudaStream_t st)
+                             uint8_t *consumed, PanelSync *sync, cudaGraphConditionalHandle cond, int set_cond,
+                             int num_sms, cudaStream_t st)
 {
-    // about one 16-byte store per thread per clear of an n-row panel
-    int64_t g = ((n + 3) / 4 * KP_MAX + 255) / 256;
+    int64_t g = (n + 255) / 256;
     if (g > 2 * num_sms) g = 2 * num_sms;
     if (g < 1) g = 1;
-    loop_step_kernel<<<(unsigned)g, 256, 0, st>>>(ls, out, init, n, status, LpT, ldL, consumed, sync, cond,
-                                                  set_cond);
+    loop_step_kernel<<<(unsigned)g, 256, 0, st>>>(ls, out, init, n, status, consumed, sync, cond, set_cond);
     return cudaGetLastError();
 }
 

@@ -102,7 +102,8 @@ struct PanelParams {
     const LoopState *ls;    // m = ls->m rows, window min(W0, m)
     FieldP f;
     int kp;                 // pivot budget of this panel (<= KP_MAX)
-    uint32_t *LpT;          // LpT[k * ldL + t]: scaled Schur column k (storage order) of compact row t
+    uint32_t *LpT;          // LpT[k * ldL + t]: scaled Schur column k (storage order) of compact row t,
+                            // for helper rows beyond the CTA's shared memory only
     uint32_t *LpC;          // LpC[k * ldL + t]: L entry of compact row t, pivot-order column k (output)
     int64_t ldL;
     uint8_t *consumed;      // [m]: partner rows taken by 2x2 pivots (zeroed)
@@ -147,11 +148,11 @@ cudaError_t launch_lw_scatter(const uint32_t *LpC, int64_t ldL, int64_t n, const
 // init != 0: start the loop at order n.  Otherwise advance it past the panel
 // in `out` (end it when nothing remains, on an abort, on an error status, or
 // if a panel retired no row), and, with set_cond, set the graph's while
-// condition to "not done".  Either way the next panel's LpT columns,
-// consumed flags and PanelSync are cleared.
+// condition to "not done".  Either way the next panel's partner flags
+// (consumed) and PanelSync are cleared.
 cudaError_t launch_loop_step(LoopState *ls, const PanelOut *out, int init, int64_t n, int32_t *status,
-                             uint32_t *LpT, int64_t ldL, uint8_t *consumed, PanelSync *sync,
-                             cudaGraphConditionalHandle cond, int set_cond, int num_sms, cudaStream_t st);
+                             uint8_t *consumed, PanelSync *sync, cudaGraphConditionalHandle cond, int set_cond,
+                             int num_sms, cudaStream_t st);
 cudaError_t launch_finalize(int64_t n, const uint32_t *Lw, int64_t ldw, const int *piv_all,
                             const uint32_t *d_all, const uint32_t *e_all, const int *zero_all,
                             const int *zero_cols, const LoopState *ls, uint32_t *A, int64_t lda,

@@ -335,7 +335,7 @@ cudaError_t enqueue_start(const Plan &c, cudaStream_t st, cudaEvent_t *ev = null
                   : launch_ingest(c.A, c.lda, c.n, c.Sbuf[0], c.ldS, c.idxb[0], c.f, st);
     if (err != cudaSuccess) return err;
     if (ev && (err = cudaEventRecord(ev[1], st)) != cudaSuccess) return err;
-    return launch_loop_step(c.ls, c.out, 1, c.n, c.status, c.LpT, c.ldS, c.consumed, c.sync, 0, 0, c.nsm, st);
+    return launch_loop_step(c.ls, c.out, 1, c.n, c.status, c.consumed, c.sync, 0, 0, c.nsm, st);
 }
 
 // One panel step on half h: pivot chain (which also appends to the pivot and
@@ -370,8 +370,7 @@ cudaError_t enqueue_step(const Plan &c, int h, cudaGraphConditionalHandle cond, 
                            g_budget_ns, c.status, c.nsm, g_test_drop == LDLT_TEST_DROP_UPDATE_COPIES, st));
     }
     if (ev) EQ(cudaEventRecord(ev[4], st));
-    EQ(launch_loop_step(c.ls, c.out, 0, c.n, c.status, c.LpT, c.ldS, c.consumed, c.sync, cond, set_cond, c.nsm,
-                        st));
+    EQ(launch_loop_step(c.ls, c.out, 0, c.n, c.status, c.consumed, c.sync, cond, set_cond, c.nsm, st));
     return cudaSuccess;
 #undef EQ
 }

@@ -442,10 +442,10 @@ __device__ void helper_cta(const PanelParams &P, Shared &sh, int lo, int hi)
             CHAIN_PROF(hmark = clock64(); hidle += hmark - tw;)
             if (blockIdx.x == 1) P.out->dbg[7] = e;
             sh.hgo = sh.ev_ready > e;  // one decision for every compute thread
+            __threadfence_block();     // the loader's column values before the barrier hands them on
         }
         cbar();
         if (!sh.hgo) { hflush(); return; }  // quit or abort
-        __threadfence_block();
         const int s = e % NSLOT;
         const int kind = sh.ev[s].kind;
         const int np = sh.ev[s].np, a = sh.ev[s].a, b = sh.ev[s].b;
@@ -478,16 +478,20 @@ __device__ void helper_cta(const PanelParams &P, Shared &sh, int lo, int hi)
                 const uint32_t c = schur2<BIG>(P, sh.U, lr, t, sa, W, za, np, half, valid, sm);
                 if (valid && half == 0) {
                     if (sm) sh.U[lr * RS + np] = c;
-                    P.LpT[(int64_t)np * P.ldL + t] = c;
+                    else P.LpT[(int64_t)np * P.ldL + t] = c;
                 }
             } else if (kind == EV_PIVOT2) {
                 const uint32_t sb = valid ? (sm ? sh.scol[s][1][lr] : s_at(P.S, P.ldS, t, b)) : 0u;
                 const uint32_t ca = schur2<BIG>(P, sh.U, lr, t, sa, W, za, np, half, valid, sm);
                 const uint32_t cb = schur2<BIG>(P, sh.U, lr, t, sb, W, zb, np, half, valid, sm);
                 if (valid && half == 0) {
-                    if (sm) { sh.U[lr * RS + np] = ca; sh.U[lr * RS + np + 1] = cb; }
-                    P.LpT[(int64_t)np * P.ldL + t] = ca;
-                    P.LpT[(int64_t)(np + 1) * P.ldL + t] = cb;
+                    if (sm) {
+                        sh.U[lr * RS + np] = ca;
+                        sh.U[lr * RS + np + 1] = cb;
+                    } else {
+                        P.LpT[(int64_t)np * P.ldL + t] = ca;
+                        P.LpT[(int64_t)(np + 1) * P.ldL + t] = cb;
+                    }
                 }
             } else {  // EV_SCAN
                 const uint32_t c = schur2<BIG>(P, sh.U, lr, t, sa, W, za, np, half, valid, sm);
@@ -774,7 +778,6 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, const int m, const 
         for (int q = tid; q < (np - npk) * w; q += NCT) {
             const int j = npk + q / w, t = q % w;
             sh.U[t * RS + j] = 0;
-            P.LpT[(int64_t)j * P.ldL + t] = 0;
         }
         np = npk;
         nzero = sh.pend_nz[slot];
@@ -884,7 +887,6 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, const int m, const 
             // ---- 1x1 pivot: U~[:, np] = c~_a, delta = W c~_a[a] ----
             if (myrow && half == 0) {
                 sh.U[lr * RS + np] = ca_t;
-                P.LpT[(int64_t)np * P.ldL + lr] = ca_t;
             }
             const uint32_t delta = fp_mul(W, caa, f);
             if (tid < np && sh.kind[tid] != K_2B) sh.bw[tid] = fp_mul(sh.bw[tid], delta, f);
@@ -1004,8 +1006,6 @@ __device__ void leader_cta(const PanelParams &P, Shared &sh, const int m, const 
         if (myrow && half == 0) {
             sh.U[lr * RS + np] = ca_t;  // c~_a[a] = 0 here
             sh.U[lr * RS + np + 1] = cb_t;
-            P.LpT[(int64_t)np * P.ldL + lr] = ca_t;
-            P.LpT[(int64_t)(np + 1) * P.ldL + lr] = cb_t;
         }
         const uint32_t delta = fp_mul(W, fp_mul(x, x, f), f);
         if (tid < np && sh.kind[tid] != K_2B) sh.bw[tid] = fp_mul(sh.bw[tid], delta, f);
