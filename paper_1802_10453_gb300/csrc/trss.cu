@@ -11,7 +11,7 @@
 //                      one row, in one CTA (x_ii = c_ii / (2 u_ii), the row
 //                      to its right, a rank-2 update of the rest of the block)
 //   trss_panel_kernel  X_k,r = U_kk^{-T} (C_k,r - X_kk^T U_k,r) for the
-//                      columns r >= k1, 64 columns per CTA
+//                      columns r >= k1, a warp per column
 //   trss_syr2k_kernel  C_r,r -= X_k,r^T U_k,r + U_k,r^T X_k,r on the upper
 //                      triangle of the trailing block, 64 x 64 tiles
 // Characteristic 2: the diagonal of X^T U + U^T X is zero, so a solution
@@ -27,7 +27,7 @@
 namespace {
 
 constexpr int TB = 32;      // rows per block step
-constexpr int TC = 64;      // columns per CTA in the panel and trailing kernels
+constexpr int TC = 64;      // columns per CTA tile of the trailing kernel
 
 __device__ __forceinline__ uint32_t rd(const uint32_t *M, int64_t ld, int64_t i, int64_t j, const FieldP &f)
 {
@@ -82,16 +82,18 @@ __global__ void __launch_bounds__(TB * TB) trss_diag_kernel(int64_t k0, int nb, 
     if (in) C[(k0 + ty) * ldc + k0 + tx] = c[ty][tx];
 }
 
-// X_k,r for the columns [c0, c0 + TC) of the trailing part, one thread per
-// column j: t = C_k,j - X_kk^T U_k,j, then U_kk^T y = t.  Every load is issued
-// first; the TRMM part is nb independent sums; the substitution runs
-// right-looking (y_i final, then subtracted from the later sums), so each of
-// its nb steps costs one reduction and one product on the dependent chain.
-// For p < 2^28 a sum of at most 2 TB products (each < 2^56) stays below 2^63
-// without folding.
+// X_k,r for the columns r >= k1 of the trailing part, one warp per column j
+// and one lane per row i of the block: t_i = C_ij - sum_{k <= i} X_ki U_kj
+// (the column of U held one entry per lane and broadcast by shuffles), then
+// U_kk^T y = t right-looking: lane i finishes y_i, it is broadcast, and the
+// lanes below add u_il y_i.  Each of the nb steps of the substitution costs
+// one reduction, one product and one shuffle on the dependent chain, and all
+// columns of the step run side by side.  For p < 2^28 a lane's sum of at most
+// 2 TB products (each < 2^56) stays below 2^63 without folding.
+constexpr int PW = 8;  // columns (warps) per CTA in the panel kernel
 template <bool BIG>
-__global__ void __launch_bounds__(TC) trss_panel_kernel(int64_t k0, int nb, int64_t n, const uint32_t *U,
-                                                         int64_t ldu, uint32_t *C, int64_t ldc, FieldP f)
+__global__ void __launch_bounds__(PW * 32) trss_panel_kernel(int64_t k0, int nb, int64_t n, const uint32_t *U,
+                                                              int64_t ldu, uint32_t *C, int64_t ldc, FieldP f)
 {
     __shared__ uint32_t u[TB][TB + 1], x[TB][TB + 1], uinv[TB];
     const int64_t k1 = k0 + nb;
@@ -107,36 +109,32 @@ __global__ void __launch_bounds__(TC) trss_panel_kernel(int64_t k0, int nb, int6
         uinv[threadIdx.x] = d ? fp_inv(d, f) : 0u;
     }
     __syncthreads();
-    const int64_t j = k1 + (int64_t)blockIdx.x * TC + threadIdx.x;
-    if (j >= n) return;
-    uint32_t uc[TB], cc[TB];
-#pragma unroll
-    for (int r = 0; r < TB; ++r) {
-        uc[r] = r < nb ? rd(U, ldu, k0 + r, j, f) : 0u;
-        cc[r] = r < nb ? rd(C, ldc, k0 + r, j, f) : 0u;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t j = k1 + (int64_t)blockIdx.x * PW + warp;
+    if (j >= n) return;  // whole warps
+    const bool row = lane < nb;
+    const uint32_t ucj = row ? rd(U, ldu, k0 + lane, j, f) : 0u;
+    const uint32_t ccj = row ? rd(C, ldc, k0 + lane, j, f) : 0u;
+    uint64_t acc = 0;
+    for (int k = 0; k < nb; ++k) {  // acc_i = sum_{k <= i} x_ki u_kj (x is upper triangular)
+        const uint32_t ukj = __shfl_sync(0xffffffffu, ucj, k);
+        if (BIG) fp_mac(acc, x[k][lane], ukj, f);
+        else acc += (uint64_t)x[k][lane] * ukj;
     }
-    uint64_t acc[TB];
-#pragma unroll
-    for (int i = 0; i < TB; ++i) {  // acc_i = sum_{k <= i} x_ki u_kj (zero rows of x past nb)
-        acc[i] = 0;
-#pragma unroll
-        for (int k = 0; k <= i; ++k) {
-            if (BIG) fp_mac(acc[i], x[k][i], uc[k], f);
-            else acc[i] += (uint64_t)x[k][i] * uc[k];
+    uint32_t y = 0;
+    for (int i = 0; i < nb; ++i) {
+        uint32_t yi = 0;
+        if (lane == i) {
+            yi = fp_mul(fp_sub(ccj, fp_reduce64(acc, f), f), uinv[i], f);
+            y = yi;
+        }
+        yi = __shfl_sync(0xffffffffu, yi, i);
+        if (lane > i) {
+            if (BIG) fp_mac(acc, u[i][lane], yi, f);
+            else acc += (uint64_t)u[i][lane] * yi;
         }
     }
-#pragma unroll
-    for (int i = 0; i < TB; ++i) {
-        if (i < nb) {
-            const uint32_t y = fp_mul(fp_sub(cc[i], fp_reduce64(acc[i], f), f), uinv[i], f);
-            C[(k0 + i) * ldc + j] = y;
-#pragma unroll
-            for (int l = i + 1; l < TB; ++l) {
-                if (BIG) fp_mac(acc[l], u[i][l], y, f);
-                else acc[l] += (uint64_t)u[i][l] * y;
-            }
-        }
-    }
+    if (row) C[(k0 + lane) * ldc + j] = y;
 }
 
 // C[i][j] -= sum_k (X[k][i] U[k][j] + U[k][i] X[k][j]) for k in the block,
@@ -222,10 +220,11 @@ extern "C" int ldlt_rpm_trss(int64_t n, uint32_t p, const uint32_t *U, int64_t l
         const int64_t rest = n - (k0 + nb);
         if (rest <= 0) continue;
         const unsigned gp = (unsigned)((rest + TC - 1) / TC);
+        const unsigned gw = (unsigned)((rest + PW - 1) / PW);
         if (p >= (1u << 28))
-            trss_panel_kernel<true><<<gp, TC, 0, st>>>(k0, nb, n, U, ldu, C, ldc, f);
+            trss_panel_kernel<true><<<gw, PW * 32, 0, st>>>(k0, nb, n, U, ldu, C, ldc, f);
         else
-            trss_panel_kernel<false><<<gp, TC, 0, st>>>(k0, nb, n, U, ldu, C, ldc, f);
+            trss_panel_kernel<false><<<gw, PW * 32, 0, st>>>(k0, nb, n, U, ldu, C, ldc, f);
         if (p >= (1u << 28))
             trss_syr2k_kernel<true><<<dim3(gp, gp), 256, 0, st>>>(k0, nb, n, U, ldu, C, ldc, f);
         else
