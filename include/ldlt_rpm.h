@@ -208,6 +208,28 @@ int ldlt_rpm_trss(int64_t n, uint32_t p, const uint32_t *U, int64_t ldu,
                   uint32_t *C, int64_t ldc, int32_t *status, void *stream);
 
 /*
+ * ldlt_rpm_trss_ws -- ldlt_rpm_trss with the trailing update of every block
+ * step (Algorithm 1's C3 - (X2^T U2 + U2^T X2), a SYR2K) on tcgen05 tensor
+ * cores: the exact bf16-limb product of ldlt_rpm_factor's level-3 update,
+ * with G = [X^T | U^T] and G D = [U^T | X^T] (K = 2 x 32 per step), written
+ * to C's upper triangle in place.  Trailing orders below 256 keep the
+ * CUDA-core update.  Same arguments, outputs and errors as ldlt_rpm_trss
+ * (bit-identical results), plus
+ *   ws, ws_bytes  device workspace of at least ldlt_rpm_trss_workspace_bytes
+ *                 bytes, 256-byte aligned, owned by the caller (limb
+ *                 operands and the update's size record);
+ *   status        also LDLT_ERR_TIMEOUT if the update kernel's bounded wait
+ *                 gave up.
+ * Returns what ldlt_rpm_trss returns, LDLT_ERR_WORKSPACE, or
+ * LDLT_ERR_NO_DEVICE if the device is not sm_103.  Five launches per 32-row
+ * block are enqueued; nothing is read back.
+ */
+int ldlt_rpm_trss_workspace_bytes(int64_t n, uint32_t p, size_t *bytes);
+int ldlt_rpm_trss_ws(int64_t n, uint32_t p, const uint32_t *U, int64_t ldu,
+                     uint32_t *C, int64_t ldc, int32_t *status, void *ws, size_t ws_bytes,
+                     void *stream);
+
+/*
  * ldlt_rpm_strict -- the strict form of a characteristic-2 factorisation
  * (Section 2.2, "Antitriangular decomposition"), in place on the outputs of
  * ldlt_rpm_factor / ldlt_rpm_factor_batched for the same A.

@@ -43,6 +43,7 @@ from .binding import (  # noqa: F401
     strict,
     solve,
     trss,
+    trss_workspace_bytes,
     LDLT_ERR_INCONSISTENT,
     LDLT_ERR_INTERNAL,
     set_wait_budget_ns,

@@ -42,7 +42,8 @@ NOALLOC_BYTES = 48 << 20
 EXPORTS = ["ldlt_rpm_workspace_bytes", "ldlt_rpm_factor", "rpm_from_factor", "ldlt_rpm_version",
            "ldlt_rpm_set_wait_budget_ns", "ldlt_rpm_set_speculation", "ldlt_rpm_factor_noalloc",
            "ldlt_rpm_factor_batched", "ldlt_rpm_batched_workspace_bytes", "ldlt_rpm_batched_set_schedule",
-           "ldlt_rpm_strict", "ldlt_rpm_solve", "ldlt_rpm_trss", "ldlt_rpm_factor_given",
+           "ldlt_rpm_strict", "ldlt_rpm_solve", "ldlt_rpm_trss", "ldlt_rpm_trss_ws",
+           "ldlt_rpm_trss_workspace_bytes", "ldlt_rpm_factor_given",
            "ldlt_rpm_given_workspace_bytes", "ldlt_rpm_test_drop"]
 TEST_DROP_SCAN_ANSWERS = 1   # LDLT_TEST_DROP_SCAN_ANSWERS
 TEST_DROP_UPDATE_COPIES = 2  # LDLT_TEST_DROP_UPDATE_COPIES
@@ -101,6 +102,10 @@ def lib():
             L.ldlt_rpm_strict.argtypes = [c_i64, c_u32, c_vp, c_i64, c_vp, c_vp, c_vp]
             L.ldlt_rpm_trss.restype = ctypes.c_int
             L.ldlt_rpm_trss.argtypes = [c_i64, c_u32, c_vp, c_i64, c_vp, c_i64, c_vp, c_vp]
+            L.ldlt_rpm_trss_ws.restype = ctypes.c_int
+            L.ldlt_rpm_trss_ws.argtypes = [c_i64, c_u32, c_vp, c_i64, c_vp, c_i64, c_vp, c_vp, c_sz, c_vp]
+            L.ldlt_rpm_trss_workspace_bytes.restype = ctypes.c_int
+            L.ldlt_rpm_trss_workspace_bytes.argtypes = [c_i64, c_u32, ctypes.POINTER(c_sz)]
             L.rpm_from_factor.restype = ctypes.c_int
             L.rpm_from_factor.argtypes = [c_i64, c_vp, c_vp, c_vp, c_vp, c_vp]
             L.ldlt_rpm_version.restype = ctypes.c_int
@@ -450,12 +455,22 @@ def strict(A, res: dict, stream=None) -> dict:
     return res
 
 
-def trss(U, C, p: int, stream=None, check: bool = True):
-    """ldlt_rpm_trss (Algorithm 1): X upper triangular with X^T U + U^T X = C.
-    U and C are square CUDA int32/uint32 tensors of the same order (U's upper
-    triangle and C's upper triangle are read); C's upper triangle is
-    overwritten by X in place.  Returns the device status tensor; with
-    check=True waits for the stream and raises if it is non-zero."""
+def trss_workspace_bytes(n: int, p: int) -> int:
+    out = ctypes.c_size_t(0)
+    rc = lib().ldlt_rpm_trss_workspace_bytes(int(n), int(p), ctypes.byref(out))
+    if rc != LDLT_OK:
+        raise LdltError(rc, "ldlt_rpm_trss_workspace_bytes")
+    return int(out.value)
+
+
+def trss(U, C, p: int, stream=None, check: bool = True, tensor: bool = True, workspace=None):
+    """ldlt_rpm_trss_ws (tensor=True, the trailing updates on tcgen05 with a
+    workspace) or ldlt_rpm_trss (CUDA-core updates), Algorithm 1: X upper
+    triangular with X^T U + U^T X = C.  U and C are square CUDA int32/uint32
+    tensors of the same order (U's upper triangle and C's upper triangle are
+    read); C's upper triangle is overwritten by X in place; both forms give
+    the same bits.  Returns the device status tensor; with check=True waits
+    for the stream and raises if it is non-zero."""
     import torch
     n = int(U.shape[0])
     if tuple(U.shape) != (n, n) or tuple(C.shape) != (n, n):
@@ -466,7 +481,14 @@ def trss(U, C, p: int, stream=None, check: bool = True):
     st = torch.zeros(1, dtype=torch.int32, device=dev)
     ldu = U.stride(0) if n > 0 else 1
     ldc = C.stride(0) if n > 0 else 1
-    rc = lib().ldlt_rpm_trss(n, int(p), U.data_ptr(), ldu, C.data_ptr(), ldc, st.data_ptr(), stream.cuda_stream)
+    if tensor:
+        if workspace is None:
+            workspace = torch.empty(trss_workspace_bytes(n, p), dtype=torch.uint8, device=dev)
+        rc = lib().ldlt_rpm_trss_ws(n, int(p), U.data_ptr(), ldu, C.data_ptr(), ldc, st.data_ptr(),
+                                    workspace.data_ptr(), workspace.numel(), stream.cuda_stream)
+    else:
+        rc = lib().ldlt_rpm_trss(n, int(p), U.data_ptr(), ldu, C.data_ptr(), ldc, st.data_ptr(),
+                                 stream.cuda_stream)
     if rc != LDLT_OK:
         raise LdltError(rc, "ldlt_rpm_trss")
     if check:

@@ -222,6 +222,8 @@ struct TcArgs {
     int64_t budget_ns;
     int32_t *status;
     int test_drop;                  // LDLT_TEST_DROP_UPDATE_COPIES: producer stops after one stage
+    int upper;                      // 1: output (i, j), j <= i, lives at S[j][i] (the upper triangle;
+                                    // S and Snext the same block, sigma the identity)
     int nst;
 };
 
@@ -390,7 +392,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1) syrdk_tc_kernel(const TcArgs ar
             // Asynchronous 4-byte copies, all in flight at once: one memory
             // round trip per tile.  S is only read in this kernel (the new
             // values go to Snext), so the L1-allocating form sees no stale line.
-            {
+            if (args.upper) {
+                // old value of output (i, j) at S[j][i]: warp wq takes the tile's
+                // columns wq*8 .. wq*8+7, lanes run along i (contiguous in S)
+#pragma unroll 2
+                for (int c = 0; c < 8; ++c) {
+                    const int jl = wq * 8 + c, j = J * BN + jl;
+                    const uint32_t *srow = args.S + (int64_t)j * args.ldS;
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        const int il = 32 * h + lane, i = I * BM + il;
+                        uint32_t *d = cg + il * CLD + jl;
+                        if (i < mn && j <= i && j < mn) cp_async4(d, srow + i);
+                        else *d = 0u;
+                    }
+                }
+                asm volatile("cp.async.commit_group;\n" ::: "memory");
+                asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+            } else {
                 const int j0 = J * BN + lane, j1 = j0 + 32;
                 const int sj0 = j0 < mn ? __ldg(args.sigma + j0) : 0;
                 const int sj1 = j1 < mn ? __ldg(args.sigma + j1) : 0;
@@ -441,7 +460,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) syrdk_tc_kernel(const TcArgs ar
                     o[e] = fp_sub(crow[c0 + e], fp_reduce64_fold((uint64_t)(v + (int64_t)bias), f), f);
                 }
                 const int jb = J * BN + c0;
-                if (i < mn) {
+                if (args.upper) {
+                    // S[j][i]: the lanes' consecutive rows i make each store one line
+                    if (i < mn) {
+#pragma unroll
+                        for (int e = 0; e < 8; ++e)
+                            if (jb + e <= i && jb + e < mn) args.Snext[(int64_t)(jb + e) * args.ldS + i] = o[e];
+                    }
+                } else if (i < mn) {
                     if (jb + 7 <= i && jb + 7 < mn) {
                         uint4 *dst = (uint4 *)(drow + jb);
                         dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
@@ -512,6 +538,51 @@ struct SplitArgs {
     __nv_bfloat16 *Aop, *Bop;
 };
 
+// Write the limb operands of row i, columns k0 .. k0+7: the digits of GD
+// (A operand) and of the pre-scaled copies of G (B operand), in the pre-tiled
+// core-matrix layouts the SYRDK kernel copies stage by stage.
+__device__ __forceinline__ void split_write(const SplitArgs &a, int i, int k0, int kpad, int kprime, int rows,
+                                            const int32_t (&gd_bal)[8], const uint32_t (&gk)[8])
+{
+    const FieldP f = a.f;
+    const int LA = a.la, LB = a.lb;
+    int32_t gb[8];
+    // A operand: digit u of GD at K' column u*kpad + k
+    const int I = i / BM, ri = i % BM;
+    const int J = i / a.bn, rj = i % a.bn;
+    int32_t dg[8][4];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) digits(gd_bal[e], LA, a.ash, dg[e]);
+    for (int u = 0; u < LA; ++u) {
+        int32_t v8[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v8[e] = dg[e][u];
+        const int kk = u * kpad + k0;
+        const int64_t off = (int64_t)I * BM * kprime + (int64_t)(kk / 8) * (BM * 8) + ri * 8;
+        *(uint4 *)(a.Aop + off) = pack8(v8);
+    }
+    // B operand: base-256 digit v of b~_u = balanced(beta^u g mod p), rows v*bn + rj
+    if (i < ((rows + a.bn - 1) / a.bn) * a.bn) {
+        for (int u = 0; u < LA; ++u) {
+            int32_t db[8][4];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                gb[e] = balanced(fp_mul(a.wbase[u], gk[e], f), f.p);
+                digits(gb[e], LB, 8, db[e]);
+            }
+            const int kk = u * kpad + k0;
+            for (int v = 0; v < LB; ++v) {
+                int32_t v8[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) v8[e] = db[e][v];
+                const int64_t off = (int64_t)J * a.nprime * kprime + (int64_t)(kk / 8) * (a.nprime * 8) +
+                                    (int64_t)(v * a.bn + rj) * 8;
+                *(uint4 *)(a.Bop + off) = pack8(v8);
+            }
+        }
+    }
+}
+
 // One thread per (row i, group of 8 columns k..k+7).
 __global__ void split_tc_kernel(const SplitArgs a)
 {
@@ -535,7 +606,7 @@ __global__ void split_tc_kernel(const SplitArgs a)
         const int k = k0 - 1 + e;
         g[e] = (i < m_next && k >= 0 && k < np) ? a.LpC[(int64_t)k * a.ldL + a.sigma[i]] : 0u;
     }
-    int32_t gd_bal[8], gb[8];
+    int32_t gd_bal[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
         const int k = k0 + e;
@@ -549,40 +620,50 @@ __global__ void split_tc_kernel(const SplitArgs a)
         }
         gd_bal[e] = balanced(v, f.p);
     }
-    // A operand: digit u of GD at K' column u*kpad + k
-    const int I = i / BM, ri = i % BM;
-    const int J = i / a.bn, rj = i % a.bn;
-    int32_t dg[8][4];
+    uint32_t gk[8];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) digits(gd_bal[e], LA, a.ash, dg[e]);
-    for (int u = 0; u < LA; ++u) {
-        int32_t v8[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) v8[e] = dg[e][u];
-        const int kk = u * kpad + k0;
-        const int64_t off = (int64_t)I * BM * kprime + (int64_t)(kk / 8) * (BM * 8) + ri * 8;
-        *(uint4 *)(a.Aop + off) = pack8(v8);
+    for (int e = 0; e < 8; ++e) gk[e] = g[e + 1];
+    split_write(a, i, k0, kpad, kprime, rows, gd_bal, gk);
+}
+
+// Operands of Algorithm 1's trailing update C_rr -= X_k,r^T U_k,r + U_k,r^T X_k,r
+// (the SYR2K of TRSS) in the SYRDK layout: for trailing row i the K = 2 nb
+// entries G[i] = [X_k,i | U_k,i] and GD[i] = [U_k,i | X_k,i] (block rows
+// k0 .. k0+nb-1, column r0 + i), so GD G^T = U^T X + X^T U.  Thread (0, 0) of
+// the grid writes the update's sizes for the SYRDK kernel.
+__global__ void trss_split_tc_kernel(const SplitArgs a, const uint32_t *__restrict__ U, int64_t ldu,
+                                     const uint32_t *__restrict__ X, int64_t ldx, int64_t k0, int nb, int64_t r0,
+                                     int m, PanelOut *out)
+{
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+        out->m_next = m;
+        out->np = 2 * nb;
+        out->abort = 0;
     }
-    // B operand: base-256 digit v of b~_u = balanced(beta^u g mod p), rows v*bn + rj
-    if (i < ((rows + a.bn - 1) / a.bn) * a.bn) {
-        for (int u = 0; u < LA; ++u) {
-            int32_t db[8][4];
+    const int np = 2 * nb;
+    const int kpad = (np + 63) / 64 * 64, rows = (m + BM - 1) / BM * BM, kprime = a.la * kpad;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k0g = blockIdx.y * 8;
+    if (i >= rows || k0g >= kpad) return;
+    const FieldP f = a.f;
+    uint32_t gk[8];
+    int32_t gd_bal[8];
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                gb[e] = balanced(fp_mul(a.wbase[u], g[e + 1], f), f.p);
-                digits(gb[e], LB, 8, db[e]);
-            }
-            const int kk = u * kpad + k0;
-            for (int v = 0; v < LB; ++v) {
-                int32_t v8[8];
-#pragma unroll
-                for (int e = 0; e < 8; ++e) v8[e] = db[e][v];
-                const int64_t off = (int64_t)J * a.nprime * kprime + (int64_t)(kk / 8) * (a.nprime * 8) +
-                                    (int64_t)(v * a.bn + rj) * 8;
-                *(uint4 *)(a.Bop + off) = pack8(v8);
-            }
+    for (int e = 0; e < 8; ++e) {
+        const int k = k0g + e;
+        uint32_t gv = 0, dv = 0;
+        if (i < m && k < np) {
+            const int kk = k < nb ? k : k - nb;
+            uint32_t xu = U[(k0 + kk) * ldu + r0 + i];
+            if (xu >= f.p) xu %= f.p;
+            const uint32_t xx = X[(k0 + kk) * ldx + r0 + i];  // X_k,r: already reduced
+            gv = k < nb ? xx : xu;
+            dv = k < nb ? xu : xx;
         }
+        gk[e] = gv;
+        gd_bal[e] = balanced(dv, f.p);
     }
+    split_write(a, i, k0g, kpad, kprime, rows, gd_bal, gk);
 }
 
 }  // namespace
@@ -664,12 +745,38 @@ cudaError_t launch_split_tc(const uint32_t *LpC, int64_t ldL, const int *sigma, 
     return cudaGetLastError();
 }
 
+cudaError_t launch_trss_split_tc(const uint32_t *U, int64_t ldu, const uint32_t *X, int64_t ldx, int64_t k0, int nb,
+                                 int64_t r0, int m, PanelOut *out, FieldP f, int limbs, void *Aop, void *Bop,
+                                 cudaStream_t st)
+{
+    if (m <= 0) return cudaSuccess;
+    SplitArgs a;
+    a.LpC = nullptr; a.ldL = 0; a.sigma = nullptr;
+    int ash = 8;
+    a.lb = limbs; a.la = tc_limbs_a(f.p, &ash); a.ash = ash; a.bn = tc_bn(limbs);
+    a.nprime = limbs * a.bn;
+    a.ls = nullptr; a.out = out; a.f = f;
+    a.S = nullptr; a.ldS = 0; a.Snext = nullptr;
+    uint64_t w = 1;
+    for (int u = 0; u < 4; ++u) {
+        a.wbase[u] = (uint32_t)(w % f.p);
+        w = (w << ash) % f.p;
+    }
+    a.Aop = (__nv_bfloat16 *)Aop;
+    a.Bop = (__nv_bfloat16 *)Bop;
+    const int kpad = (2 * nb + 63) / 64 * 64;
+    dim3 grid((unsigned)((round_up(m, BM) + 127) / 128), (unsigned)(kpad / 8));
+    trss_split_tc_kernel<<<grid, 128, 0, st>>>(a, U, ldu, X, ldx, k0, nb, r0, m, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_syrdk_tc(const uint32_t *S, int64_t ldS, const int *sigma, const LoopState *ls,
                             const PanelOut *out, const void *Aop, const void *Bop, int limbs, FieldP f,
                             uint32_t *Snext, int64_t budget_ns, int32_t *status, int num_sms,
-                            int test_drop, cudaStream_t st)
+                            int test_drop, cudaStream_t st, int upper)
 {
     TcArgs a;
+    a.upper = upper;
     a.S = S; a.ldS = ldS; a.sigma = sigma; a.ls = ls; a.out = out;
     a.Aop = (const __nv_bfloat16 *)Aop; a.Bop = (const __nv_bfloat16 *)Bop;
     int ash = 8;

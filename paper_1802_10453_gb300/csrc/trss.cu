@@ -200,7 +200,112 @@ __global__ void __launch_bounds__(256) trss_syr2k_kernel(int64_t k0, int nb, int
         }
 }
 
+__global__ void trss_iota_kernel(int *sigma, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        sigma[i] = (int)i;
+}
+
+constexpr int TRSS_TC_MIN = 256;  // trailing orders below this keep the CUDA-core SYR2K
+
+// Workspace of the tensor-core form: loop state and update record (read by
+// the SYRDK kernel), the identity row map, the limb operands.
+struct TrssLayout {
+    size_t ls, out, sigma, opA, opB, total;
+};
+
+void trss_layout(int64_t n, uint32_t p, TrssLayout &L)
+{
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += (bytes + 255) / 256 * 256;
+        return o;
+    };
+    const int limbs = tc_limbs(p);
+    L.ls = take(sizeof(LoopState));
+    L.out = take(sizeof(PanelOut));
+    L.sigma = take((size_t)(n > 0 ? n : 1) * 4);
+    const int64_t nn = n > 0 ? n : 1;
+    L.opA = take(tc_operand_bytes(nn, limbs));
+    L.opB = L.opA + (size_t)round_up(round_up(nn, 128) * (int64_t)limbs * KP_MAX * 2, 256);
+    L.total = off;
+}
+
 }  // namespace
+
+extern "C" int ldlt_rpm_trss_workspace_bytes(int64_t n, uint32_t p, size_t *bytes)
+{
+    size_t tmp = 0;
+    const int rc = ldlt_rpm_workspace_bytes(1, p, LDLT_PATH_TC, &tmp);  // p prime, in range
+    if (rc != LDLT_OK) return rc;
+    if (n < 0 || !bytes) return LDLT_ERR_ARG;
+    TrssLayout L;
+    trss_layout(n, p, L);
+    *bytes = L.total;
+    return LDLT_OK;
+}
+
+extern "C" int ldlt_rpm_trss_ws(int64_t n, uint32_t p, const uint32_t *U, int64_t ldu, uint32_t *C, int64_t ldc,
+                                int32_t *status, void *ws, size_t ws_bytes, void *stream)
+{
+    size_t need = 0;
+    const int rc = ldlt_rpm_trss_workspace_bytes(n, p, &need);
+    if (rc != LDLT_OK) return rc;
+    if (!status) return LDLT_ERR_ARG;
+    if (!ws || ws_bytes < need || ((uintptr_t)ws & 255) != 0) return LDLT_ERR_WORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(status, 0, sizeof(int32_t), st) != cudaSuccess) return LDLT_ERR_CUDA;
+    if (n == 0) return LDLT_OK;
+    if (!U || !C || ldu < n || ldc < n) return LDLT_ERR_ARG;
+    int dev = 0, nsm = 0, major = 0, minor = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess)
+        return LDLT_ERR_CUDA;
+    if (major != 10 || minor != 3) return LDLT_ERR_NO_DEVICE;
+    TrssLayout Lo;
+    trss_layout(n, p, Lo);
+    uint8_t *w = (uint8_t *)ws;
+    LoopState *ls = (LoopState *)(w + Lo.ls);
+    PanelOut *out = (PanelOut *)(w + Lo.out);
+    int *sigma = (int *)(w + Lo.sigma);
+    void *opA = w + Lo.opA, *opB = w + Lo.opB;
+    const FieldP f = make_field(p);
+    const int limbs = tc_limbs(p);
+    // loop state "running" and an update record with no abort: the SYRDK kernel's liveness test
+    if (cudaMemsetAsync(w, 0, Lo.sigma, st) != cudaSuccess) return LDLT_ERR_CUDA;
+    trss_iota_kernel<<<(unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), 256, 0, st>>>(sigma, n);
+    for (int64_t k0 = 0; k0 < n; k0 += TB) {
+        const int nb = (int)((n - k0) < TB ? (n - k0) : TB);
+        trss_diag_kernel<<<1, TB * TB, 0, st>>>(k0, nb, U, ldu, C, ldc, status, f);
+        const int64_t k1 = k0 + nb, rest = n - k1;
+        if (rest <= 0) continue;
+        const unsigned gw = (unsigned)((rest + PW - 1) / PW);
+        if (p >= (1u << 28))
+            trss_panel_kernel<true><<<gw, PW * 32, 0, st>>>(k0, nb, n, U, ldu, C, ldc, f);
+        else
+            trss_panel_kernel<false><<<gw, PW * 32, 0, st>>>(k0, nb, n, U, ldu, C, ldc, f);
+        if (rest >= TRSS_TC_MIN) {
+            // C_rr -= X^T U + U^T X on tensor cores: the SYRDK kernel on C's upper triangle
+            if (launch_trss_split_tc(U, ldu, C, ldc, k0, nb, k1, (int)rest, out, f, limbs, opA, opB, st) !=
+                cudaSuccess)
+                return LDLT_ERR_CUDA;
+            uint32_t *blk = C + k1 * ldc + k1;
+            if (launch_syrdk_tc(blk, ldc, sigma, ls, out, opA, opB, limbs, f, blk, 2000000000LL, status, nsm, 0,
+                                st, 1) != cudaSuccess)
+                return LDLT_ERR_CUDA;
+        } else {
+            const unsigned gp = (unsigned)((rest + TC - 1) / TC);
+            if (p >= (1u << 28))
+                trss_syr2k_kernel<true><<<dim3(gp, gp), 256, 0, st>>>(k0, nb, n, U, ldu, C, ldc, f);
+            else
+                trss_syr2k_kernel<false><<<dim3(gp, gp), 256, 0, st>>>(k0, nb, n, U, ldu, C, ldc, f);
+        }
+    }
+    return cudaGetLastError() == cudaSuccess ? LDLT_OK : LDLT_ERR_CUDA;
+}
 
 extern "C" int ldlt_rpm_trss(int64_t n, uint32_t p, const uint32_t *U, int64_t ldu, uint32_t *C, int64_t ldc,
                              int32_t *status, void *stream)

@@ -35,12 +35,12 @@ def _inputs(n, p, seed, zero_diag_c=False):
     return U, C
 
 
-def _gpu(U, C, p, check=True):
+def _gpu(U, C, p, check=True, tensor=True):
     Ud = torch.from_numpy(U.astype(np.uint32).view(np.int32)).cuda()
     low = np.tril(C, -1) + 7  # marker values in the strict lower triangle
     Cin = np.triu(C) + np.tril(low, -1)
     Cd = torch.from_numpy(Cin.astype(np.uint32).view(np.int32)).cuda()
-    st = lr.trss(Ud, Cd, p, check=check)
+    st = lr.trss(Ud, Cd, p, check=check, tensor=tensor)
     torch.cuda.synchronize()
     out = Cd.cpu().numpy().view(np.uint32).astype(np.int64)
     assert np.array_equal(np.tril(out, -1), np.tril(Cin, -1))  # lower triangle untouched
@@ -82,6 +82,26 @@ def test_trss_identity_larger(n, p):
     assert not np.any(np.tril(X, -1))
     lhs = (o.matmul_mod(X.T, U, p) + o.matmul_mod(U.T, X, p)) % p
     assert np.array_equal(lhs, C)
+
+
+@pytest.mark.parametrize("n,p", [(257, 3), (600, 65521), (300, 2), (513, 8388593), (1000, 2147483647),
+                                 (700, 67108859)])
+def test_trss_tensor_update_equals_cuda_core(n, p):
+    """The tcgen05 trailing update (orders >= 256: tile tails, several block
+    steps on tensor cores, the last ones on CUDA cores) gives the same X bit
+    for bit as the CUDA-core form, which the oracle pins at small orders; for
+    odd p the identity X^T U + U^T X = C holds exactly."""
+    if p == 2:
+        U, _ = _inputs(n, 2, 9 + n)
+        Y = np.triu(np.random.default_rng(n).integers(0, 2, size=(n, n)))
+        C = (o.matmul_mod(Y.T, U, 2) + o.matmul_mod(U.T, Y, 2)) % 2
+    else:
+        U, C = _inputs(n, p, 31 * n + p % 97)
+    Xt, st = _gpu(U, C, p, tensor=True)
+    Xc, sc = _gpu(U, C, p, tensor=False)
+    assert st == sc == 0
+    assert np.array_equal(Xt, Xc)
+    assert np.array_equal((o.matmul_mod(Xt.T, U, p) + o.matmul_mod(U.T, Xt, p)) % p, C)
 
 
 def test_trss_reports_zero_diagonal_and_bad_arguments():
