@@ -35,15 +35,23 @@ __device__ __forceinline__ uint32_t rd(const uint32_t *M, int64_t ld, int64_t i,
     return v >= f.p ? v % f.p : v;
 }
 
-// X_kk: TB x TB (nb x nb used) in one CTA of TB * TB threads.
+// X_kk: TB x TB (nb x nb used) in one CTA of TB * TB threads.  Thread (r, l)
+// (warp r, lane l) owns c_rl (r <= l) and the sum of the rank-2 terms it has
+// received.  Step i: warp i finishes row i of X (lane i forms x_ii, a shuffle
+// broadcasts it, x_il = (c_il - x_ii u_il) / u_ii) and stores it; after one
+// barrier every later row r adds x_ir u_il + u_ir x_il to its sum, which is
+// reduced only when its row comes.  For p < 2^28 the sums of at most 2 TB
+// products (each < 2^56) stay below 2^63; larger p fold after every product.
+template <bool BIG>
 __global__ void __launch_bounds__(TB * TB) trss_diag_kernel(int64_t k0, int nb, const uint32_t *U, int64_t ldu,
                                                             uint32_t *C, int64_t ldc, int32_t *status, FieldP f)
 {
-    __shared__ uint32_t u[TB][TB + 1], c[TB][TB + 1], uinv[TB];
-    const int tx = threadIdx.x % TB, ty = threadIdx.x / TB;  // (row ty, column tx)
-    const bool in = ty < nb && tx < nb && ty <= tx;
-    u[ty][tx] = in ? rd(U, ldu, k0 + ty, k0 + tx, f) : 0u;
-    c[ty][tx] = in ? rd(C, ldc, k0 + ty, k0 + tx, f) : 0u;
+    __shared__ uint32_t u[TB][TB + 1], x[TB][TB + 1], uinv[TB];
+    const int l = threadIdx.x % TB, r = threadIdx.x / TB;
+    const bool in = r < nb && l < nb && r <= l;
+    u[r][l] = in ? rd(U, ldu, k0 + r, k0 + l, f) : 0u;
+    const uint32_t crl = in ? rd(C, ldc, k0 + r, k0 + l, f) : 0u;
+    x[r][l] = 0u;
     __syncthreads();
     if (threadIdx.x < nb) {
         const uint32_t d = u[threadIdx.x][threadIdx.x];
@@ -55,31 +63,35 @@ __global__ void __launch_bounds__(TB * TB) trss_diag_kernel(int64_t k0, int nb, 
         }
     }
     __syncthreads();
+    uint64_t acc = 0;
     for (int i = 0; i < nb; ++i) {
-        // x_ii, then the rest of row i: x_ij = (c_ij - x_ii u_ij) / u_ii
-        __shared__ uint32_t xii;
-        if (threadIdx.x == 0) {
-            const uint32_t cii = c[i][i];
-            if (f.p == 2u) {
-                if (cii != 0u) atomicExch(status, LDLT_ERR_INCONSISTENT);
-                xii = 0u;
-            } else {
-                xii = fp_mul(fp_mul(cii, f.inv2, f), uinv[i], f);
+        if (r == i) {
+            const uint32_t ci = fp_sub(crl, fp_reduce64(acc, f), f);  // c_il after steps < i
+            uint32_t xii = 0;
+            if (l == i) {
+                if (f.p == 2u) {
+                    if (ci != 0u) atomicExch(status, LDLT_ERR_INCONSISTENT);
+                } else {
+                    xii = fp_mul(fp_mul(ci, f.inv2, f), uinv[i], f);
+                }
             }
-            c[i][i] = xii;
+            xii = __shfl_sync(0xffffffffu, xii, i);
+            uint32_t xil = 0;
+            if (l == i) xil = xii;
+            else if (l > i && l < nb) xil = fp_mul(fp_sub(ci, fp_mul(xii, u[i][l], f), f), uinv[i], f);
+            x[i][l] = xil;
         }
         __syncthreads();
-        if (ty == 0 && tx > i && tx < nb)
-            c[i][tx] = fp_mul(fp_sub(c[i][tx], fp_mul(xii, u[i][tx], f), f), uinv[i], f);
-        __syncthreads();
-        // rank-2 update of rows and columns > i: c_jl -= x_ij u_il + u_ij x_il
-        if (ty > i && ty <= tx && tx < nb) {
-            const uint64_t s = (uint64_t)c[i][ty] * u[i][tx] + (uint64_t)u[i][ty] * c[i][tx];
-            c[ty][tx] = fp_sub(c[ty][tx], fp_reduce64(s, f), f);
+        if (r > i && r <= l && l < nb) {
+            if (BIG) {
+                fp_mac(acc, x[i][r], u[i][l], f);
+                fp_mac(acc, u[i][r], x[i][l], f);
+            } else {
+                acc += (uint64_t)x[i][r] * u[i][l] + (uint64_t)u[i][r] * x[i][l];
+            }
         }
-        __syncthreads();
     }
-    if (in) C[(k0 + ty) * ldc + k0 + tx] = c[ty][tx];
+    if (in) C[(k0 + r) * ldc + k0 + l] = x[r][l];
 }
 
 // X_k,r for the columns r >= k1 of the trailing part, one warp per column j
@@ -279,7 +291,8 @@ extern "C" int ldlt_rpm_trss_ws(int64_t n, uint32_t p, const uint32_t *U, int64_
     trss_iota_kernel<<<(unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), 256, 0, st>>>(sigma, n);
     for (int64_t k0 = 0; k0 < n; k0 += TB) {
         const int nb = (int)((n - k0) < TB ? (n - k0) : TB);
-        trss_diag_kernel<<<1, TB * TB, 0, st>>>(k0, nb, U, ldu, C, ldc, status, f);
+        if (p >= (1u << 28)) trss_diag_kernel<true><<<1, TB * TB, 0, st>>>(k0, nb, U, ldu, C, ldc, status, f);
+        else trss_diag_kernel<false><<<1, TB * TB, 0, st>>>(k0, nb, U, ldu, C, ldc, status, f);
         const int64_t k1 = k0 + nb, rest = n - k1;
         if (rest <= 0) continue;
         const unsigned gw = (unsigned)((rest + PW - 1) / PW);
@@ -321,7 +334,8 @@ extern "C" int ldlt_rpm_trss(int64_t n, uint32_t p, const uint32_t *U, int64_t l
     const FieldP f = make_field(p);
     for (int64_t k0 = 0; k0 < n; k0 += TB) {
         const int nb = (int)((n - k0) < TB ? (n - k0) : TB);
-        trss_diag_kernel<<<1, TB * TB, 0, st>>>(k0, nb, U, ldu, C, ldc, status, f);
+        if (p >= (1u << 28)) trss_diag_kernel<true><<<1, TB * TB, 0, st>>>(k0, nb, U, ldu, C, ldc, status, f);
+        else trss_diag_kernel<false><<<1, TB * TB, 0, st>>>(k0, nb, U, ldu, C, ldc, status, f);
         const int64_t rest = n - (k0 + nb);
         if (rest <= 0) continue;
         const unsigned gp = (unsigned)((rest + TC - 1) / TC);
