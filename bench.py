@@ -741,23 +741,31 @@ def main():
         Ut.diagonal().copy_(torch.randint(1, pt, (nt,), dtype=torch.int32, device=dev, generator=gen))
         C0 = torch.randint(0, pt, (nt, nt), dtype=torch.int32, device=dev, generator=gen)
         Ct = torch.empty_like(C0)
-        ms_t = []
-        for it in range(4):
-            Ct.copy_(C0)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            st_t = lr.trss(Ut, Ct, pt, stream=stream, check=False)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            if it:
-                ms_t.append(e0.elapsed_time(e1))
-        ms_tr = statistics.median(ms_t)
+        wst = torch.empty(lr.trss_workspace_bytes(nt, pt), dtype=torch.uint8, device=dev)
+        forms = {}
+        for tensor in (True, False):
+            ms_t = []
+            for it in range(4):
+                Ct.copy_(C0)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                st_t = lr.trss(Ut, Ct, pt, stream=stream, check=False, tensor=tensor, workspace=wst)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if it:
+                    ms_t.append(e0.elapsed_time(e1))
+            forms[tensor] = (statistics.median(ms_t), int(st_t.item()), torch.triu(Ct).clone())
+        ms_tr = forms[True][0]
         macs = nt ** 3 / 3.0  # the SYR2K updates dominate: sum over blocks of b (n - k)^2
         trss_line = {"n": nt, "p": pt, "ms": ms_tr, "gmac_per_s": macs / (ms_tr * 1e-3) / 1e9,
-                     "status": int(st_t.item()),
-                     "form": "blocked right-looking (32-row blocks): diagonal TRSS, panel TRMM+TRSM, "
-                             "SYR2K on CUDA cores, 64-bit exact accumulation"}
+                     "status": forms[True][1],
+                     "form": "blocked right-looking (32-row blocks): diagonal TRSS, panel TRMM+TRSM "
+                             "(a warp per column), trailing SYR2K on tcgen05 (bf16 limbs, exact) for "
+                             "orders >= 256, CUDA cores below",
+                     "cuda_core_form": {"ms": forms[False][0], "status": forms[False][1]},
+                     "bit_exact_vs_cuda_core_form": bool(torch.equal(forms[True][2], forms[False][2]))}
+        del wst, forms
 
     batched = None
     if rank == 0 and not args.no_batched:
