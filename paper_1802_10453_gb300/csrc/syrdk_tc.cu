@@ -32,12 +32,13 @@
 #include <cuda_bf16.h>
 
 #include "ldlt_internal.cuh"
+#include "tc_split.cuh"
 
 #define LDLT_ERR_TIMEOUT_CODE (-6)
 
 namespace {
 
-constexpr int BM = 128;            // rows per output tile (MMA M)
+constexpr int BM = TC_BM;          // rows per output tile (MMA M)
 constexpr int BN = 64;             // output columns per tile (N' = L * BN <= 256)
 constexpr int CLD = BN + 4;        // row stride (words) of a prefetched tile of old values
 constexpr int KST = 64;            // K' elements per pipeline stage
@@ -492,97 +493,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) syrdk_tc_kernel(const TcArgs ar
 }
 
 // ---------------------------------------------------------------------------
-// operand preparation
+// operand preparation (split_write and its digit helpers: tc_split.cuh)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int32_t balanced(uint32_t x, uint32_t p)
-{
-    return x > (p >> 1) ? (int32_t)((int64_t)x - (int64_t)p) : (int32_t)x;
-}
-
-// digit u of the balanced base-2^sh expansion (top digit takes the rest)
-__device__ __forceinline__ void digits(int32_t x, int L, int sh, int32_t *d)
-{
-    const int32_t half = 1 << (sh - 1), mask = (1 << sh) - 1;
-    for (int u = 0; u < L - 1; ++u) {
-        int32_t lo = ((x + half) & mask) - half;
-        d[u] = lo;
-        x = (x - lo) >> sh;
-    }
-    d[L - 1] = x;
-}
-
-__device__ __forceinline__ uint4 pack8(const int32_t *v)
-{
-    uint32_t w[4];
-#pragma unroll
-    for (int h = 0; h < 4; ++h) {
-        __nv_bfloat16 lo = __float2bfloat16_rn((float)v[2 * h]);
-        __nv_bfloat16 hi = __float2bfloat16_rn((float)v[2 * h + 1]);
-        w[h] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
-    }
-    return make_uint4(w[0], w[1], w[2], w[3]);
-}
-
-struct SplitArgs {
-    const uint32_t *LpC;
-    int64_t ldL;
-    const int *sigma;
-    int la, ash, lb, bn, nprime;  // A: la digits of base 2^ash
-    const LoopState *ls;          // with out: m_next rows, np columns
-    const PanelOut *out;
-    const uint32_t *S;            // np = 0: Snext = S[sigma, sigma]
-    int64_t ldS;
-    uint32_t *Snext;
-    FieldP f;
-    uint32_t wbase[4];  // beta^u mod p
-    __nv_bfloat16 *Aop, *Bop;
-};
-
-// Write the limb operands of row i, columns k0 .. k0+7: the digits of GD
-// (A operand) and of the pre-scaled copies of G (B operand), in the pre-tiled
-// core-matrix layouts the SYRDK kernel copies stage by stage.
-__device__ __forceinline__ void split_write(const SplitArgs &a, int i, int k0, int kpad, int kprime, int rows,
-                                            const int32_t (&gd_bal)[8], const uint32_t (&gk)[8])
-{
-    const FieldP f = a.f;
-    const int LA = a.la, LB = a.lb;
-    int32_t gb[8];
-    // A operand: digit u of GD at K' column u*kpad + k
-    const int I = i / BM, ri = i % BM;
-    const int J = i / a.bn, rj = i % a.bn;
-    int32_t dg[8][4];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) digits(gd_bal[e], LA, a.ash, dg[e]);
-    for (int u = 0; u < LA; ++u) {
-        int32_t v8[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) v8[e] = dg[e][u];
-        const int kk = u * kpad + k0;
-        const int64_t off = (int64_t)I * BM * kprime + (int64_t)(kk / 8) * (BM * 8) + ri * 8;
-        *(uint4 *)(a.Aop + off) = pack8(v8);
-    }
-    // B operand: base-256 digit v of b~_u = balanced(beta^u g mod p), rows v*bn + rj
-    if (i < ((rows + a.bn - 1) / a.bn) * a.bn) {
-        for (int u = 0; u < LA; ++u) {
-            int32_t db[8][4];
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                gb[e] = balanced(fp_mul(a.wbase[u], gk[e], f), f.p);
-                digits(gb[e], LB, 8, db[e]);
-            }
-            const int kk = u * kpad + k0;
-            for (int v = 0; v < LB; ++v) {
-                int32_t v8[8];
-#pragma unroll
-                for (int e = 0; e < 8; ++e) v8[e] = db[e][v];
-                const int64_t off = (int64_t)J * a.nprime * kprime + (int64_t)(kk / 8) * (a.nprime * 8) +
-                                    (int64_t)(v * a.bn + rj) * 8;
-                *(uint4 *)(a.Bop + off) = pack8(v8);
-            }
-        }
-    }
-}
-
 // One thread per (row i, group of 8 columns k..k+7).
 __global__ void split_tc_kernel(const SplitArgs a)
 {
@@ -599,7 +511,6 @@ __global__ void split_tc_kernel(const SplitArgs a)
     const int k0 = blockIdx.y * 8;
     if (i >= rows || k0 >= kpad) return;
     const FieldP f = a.f;
-    const int LA = a.la, LB = a.lb;
     uint32_t g[10];  // g[1 + e] = G[i][k0 + e], e in [-1, 8]
 #pragma unroll
     for (int e = 0; e < 10; ++e) {
@@ -743,6 +654,25 @@ cudaError_t launch_split_tc(const uint32_t *LpC, int64_t ldL, const int *sigma, 
     dim3 grid((unsigned)((round_up(n, BM) + 127) / 128), KP_MAX / 8);
     split_tc_kernel<<<grid, 128, 0, st>>>(a);
     return cudaGetLastError();
+}
+
+SplitArgs tc_split_args(FieldP f, int limbs, void *Aop, void *Bop)
+{
+    SplitArgs a;
+    a.LpC = nullptr; a.ldL = 0; a.sigma = nullptr;
+    int ash = 8;
+    a.lb = limbs; a.la = tc_limbs_a(f.p, &ash); a.ash = ash; a.bn = tc_bn(limbs);
+    a.nprime = limbs * a.bn;
+    a.ls = nullptr; a.out = nullptr; a.f = f;
+    a.S = nullptr; a.ldS = 0; a.Snext = nullptr;
+    uint64_t w = 1;
+    for (int u = 0; u < 4; ++u) {
+        a.wbase[u] = (uint32_t)(w % f.p);
+        w = (w << ash) % f.p;
+    }
+    a.Aop = (__nv_bfloat16 *)Aop;
+    a.Bop = (__nv_bfloat16 *)Bop;
+    return a;
 }
 
 cudaError_t launch_trss_split_tc(const uint32_t *U, int64_t ldu, const uint32_t *X, int64_t ldx, int64_t k0, int nb,

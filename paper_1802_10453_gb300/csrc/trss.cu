@@ -23,6 +23,7 @@
 
 #include "../../include/ldlt_rpm.h"
 #include "ldlt_internal.cuh"
+#include "tc_split.cuh"
 
 namespace {
 
@@ -212,6 +213,175 @@ __global__ void __launch_bounds__(256) trss_syr2k_kernel(int64_t k0, int nb, int
         }
 }
 
+// Per diagonal entry of U, once per call (every block step reads them):
+// 1 / u_ii and h_i = 1 / (2 u_ii) (0 for p = 2), each with its Shoup
+// companion, at dq[4 i .. 4 i + 3] = {1/u_ii, companion, h_i, companion}.  A
+// zero diagonal entry is reported as LDLT_ERR_ARG.
+__global__ void trss_uinv_kernel(const uint32_t *U, int64_t ldu, int64_t n, uint4 *dq, int32_t *status, FieldP f)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t d = rd(U, ldu, i, i, f);
+        if (d == 0u) atomicCAS(status, 0, LDLT_ERR_ARG);
+        const uint32_t ui = d ? fp_inv(d, f) : 0u;
+        const uint32_t h = fp_mul(ui, f.inv2, f);
+        dq[i] = make_uint4(ui, fp_shoup_pre(ui, f), h, fp_shoup_pre(h, f));
+    }
+}
+
+// One block step of the tensor-core form in one launch: every CTA solves the
+// diagonal block X_kk (the same nb-step substitution as trss_diag_kernel, in
+// shared memory; the CTAs agree bit for bit), then each of its TB warps
+// solves one column j >= k1 of the panel X_k,r as trss_panel_kernel does, and
+// (SPLIT) the CTA writes its TB rows i = j - k1 of the trailing update's limb
+// operands, G[i] = [X_k,i | U_k,i] and GD[i] = [U_k,i | X_k,i], so that
+// GD G^T = U^T X + X^T U (rows past the last column are the zero rows that
+// pad the operands to 128).  C_kk is read by every CTA, so X_kk is not
+// written back here: CTA 0 keeps it in xcur and the next step's CTA 0 (which
+// does not read block k) stores it into C; a launch with no trailing columns
+// (the last block, one CTA) stores its own.
+//
+// The dependent chain of a substitution step uses products by residues that
+// are fixed for the step (1/u_ii, 1/(2 u_ii), u_il / u_ii), so they are
+// Shoup products with precomputed companions: x_ii = c_ii h_i and
+// x_il = c_il / u_ii - x_ii (u_il / u_ii), two products on the chain.
+struct TrssStep {
+    int64_t k0, n, ldu, ldc;
+    int nb;
+    const uint32_t *U;
+    const uint4 *dq;        // per diagonal entry: 1/u_ii, h_i and companions
+    uint32_t *C;
+    int32_t *status;
+    FieldP f;
+    const uint32_t *xprev;  // X of the previous block (TB x TB, row-major), or null
+    int64_t kprev;
+    int nbprev;
+    uint32_t *xcur;         // this block's X for the next step
+    SplitArgs sa;           // SPLIT: operand buffers and digit bases
+    PanelOut *out;          // SPLIT: the update record the SYRDK kernel reads
+};
+
+template <bool BIG, bool SPLIT>
+__global__ void __launch_bounds__(TB * TB) trss_step_kernel(const TrssStep s)
+{
+    __shared__ uint32_t u[TB][TB + 1], x[TB][TB + 1], v[TB][TB + 1], vq[TB][TB + 1];
+    __shared__ uint32_t ys[TB][TB + 1], us[TB][TB + 1];
+    __shared__ uint4 dq[TB];
+    const FieldP f = s.f;
+    const int nb = s.nb;
+    const int64_t k0 = s.k0, k1 = k0 + nb, rest = s.n - k1;
+    const int l = threadIdx.x % TB, r = threadIdx.x / TB;
+    if (blockIdx.x == 0 && s.xprev && r < s.nbprev && l < s.nbprev && r <= l)
+        s.C[(s.kprev + r) * s.ldc + s.kprev + l] = s.xprev[r * TB + l];
+    const bool in = r < nb && l < nb && r <= l;
+    const uint32_t url = in ? rd(s.U, s.ldu, k0 + r, k0 + l, f) : 0u;
+    const uint32_t crl = in ? rd(s.C, s.ldc, k0 + r, k0 + l, f) : 0u;
+    const uint4 dr = r < nb ? s.dq[k0 + r] : make_uint4(0, 0, 0, 0);
+    u[r][l] = url;
+    x[r][l] = 0u;
+    {
+        const uint32_t vr = fp_mul(url, dr.x, f);  // u_rl / u_rr
+        v[r][l] = vr;
+        vq[r][l] = fp_shoup_pre(vr, f);
+    }
+    if (l == 0) dq[r] = dr;
+    __syncthreads();
+    // ---- X_kk ----
+    uint64_t acc = 0;
+    for (int i = 0; i < nb; ++i) {
+        if (r == i) {
+            const uint32_t ci = fp_sub(crl, fp_reduce64_fold(acc, f), f);  // c_il after steps < i
+            uint32_t xii = 0;
+            if (l == i) {
+                if (f.p == 2u) {
+                    if (ci != 0u && blockIdx.x == 0) atomicCAS(s.status, 0, LDLT_ERR_INCONSISTENT);
+                } else {
+                    xii = fp_mul_shoup(ci, dr.z, dr.w, f);
+                }
+            }
+            const uint32_t ciu = fp_mul_shoup(ci, dr.x, dr.y, f);  // off the chain of x_ii
+            xii = __shfl_sync(0xffffffffu, xii, i);
+            uint32_t xil = 0;
+            if (l == i) xil = xii;
+            else if (l > i && l < nb) xil = fp_sub(ciu, fp_mul_shoup(xii, v[i][l], vq[i][l], f), f);
+            x[i][l] = xil;
+        }
+        // rows < i are final: their warps have left, warps i .. TB-1 meet
+        asm volatile("bar.sync 1, %0;" ::"r"((TB - i) * 32) : "memory");
+        if (r == i) break;  // row i is done
+        if (r <= l && l < nb) {
+            if (BIG) {
+                fp_mac(acc, x[i][r], u[i][l], f);
+                fp_mac(acc, u[i][r], x[i][l], f);
+            } else {
+                acc += (uint64_t)x[i][r] * u[i][l] + (uint64_t)u[i][r] * x[i][l];
+            }
+        }
+    }
+    __syncthreads();
+    if (blockIdx.x == 0 && in) {
+        if (rest > 0) s.xcur[r * TB + l] = x[r][l];
+        else s.C[(k0 + r) * s.ldc + k0 + l] = x[r][l];
+    }
+    // ---- panel column j (warp r, lane l = block row) ----
+    const int warp = r, lane = l;
+    const int64_t i = (int64_t)blockIdx.x * TB + warp;  // trailing index
+    const int64_t j = k1 + i;
+    uint32_t y = 0, ucj = 0;
+    if (i < rest) {
+        const bool row = lane < nb;
+        ucj = row ? rd(s.U, s.ldu, k0 + lane, j, f) : 0u;
+        const uint32_t ccj = row ? rd(s.C, s.ldc, k0 + lane, j, f) : 0u;
+        uint64_t a2 = 0;
+        for (int k = 0; k < nb; ++k) {  // sum_{k <= lane} x_k,lane u_kj (x is upper triangular)
+            const uint32_t ukj = __shfl_sync(0xffffffffu, ucj, k);
+            if (BIG) fp_mac(a2, x[k][lane], ukj, f);
+            else a2 += (uint64_t)x[k][lane] * ukj;
+        }
+        const uint4 dl = dq[lane];
+        for (int q = 0; q < nb; ++q) {
+            uint32_t yq = 0;
+            if (lane == q) {
+                yq = fp_mul_shoup(fp_sub(ccj, fp_reduce64_fold(a2, f), f), dl.x, dl.y, f);
+                y = yq;
+            }
+            yq = __shfl_sync(0xffffffffu, yq, q);
+            if (lane > q) {
+                if (BIG) fp_mac(a2, u[q][lane], yq, f);
+                else a2 += (uint64_t)u[q][lane] * yq;
+            }
+        }
+        if (row) s.C[(k0 + lane) * s.ldc + j] = y;
+    }
+    if (SPLIT) {
+        const int np = 2 * nb, kpad = (np + 63) / 64 * 64;
+        const int rows = (int)((rest + TC_BM - 1) / TC_BM * TC_BM), kprime = s.sa.la * kpad;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            s.out->m_next = (int)rest;
+            s.out->np = np;
+            s.out->abort = 0;
+        }
+        ys[warp][lane] = y;
+        us[warp][lane] = ucj;
+        __syncthreads();
+        // thread t < TB * kpad / 8 forms columns 8g .. 8g+7 (g = t mod kpad/8) of
+        // the CTA's row t / (kpad/8): G = [X | U], GD = [U | X]
+        const int ng = kpad / 8;
+        const int t = threadIdx.x, w = t / ng, g = t % ng;
+        const int64_t iw = (int64_t)blockIdx.x * TB + w;
+        if (w < TB && iw < rows) {
+            int32_t gd_bal[8];
+            uint32_t gk[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int k = 8 * g + e;
+                gk[e] = k < nb ? ys[w][k] : (k < np ? us[w][k - nb] : 0u);
+                gd_bal[e] = balanced(k < nb ? us[w][k] : (k < np ? ys[w][k - nb] : 0u), f.p);
+            }
+            split_write(s.sa, (int)iw, 8 * g, kpad, kprime, rows, gd_bal, gk);
+        }
+    }
+}
+
 __global__ void trss_iota_kernel(int *sigma, int64_t n)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -223,7 +393,7 @@ constexpr int TRSS_TC_MIN = 256;  // trailing orders below this keep the CUDA-co
 // Workspace of the tensor-core form: loop state and update record (read by
 // the SYRDK kernel), the identity row map, the limb operands.
 struct TrssLayout {
-    size_t ls, out, sigma, opA, opB, total;
+    size_t ls, out, sigma, uinv, xblk, opA, opB, total;
 };
 
 void trss_layout(int64_t n, uint32_t p, TrssLayout &L)
@@ -239,6 +409,8 @@ void trss_layout(int64_t n, uint32_t p, TrssLayout &L)
     L.out = take(sizeof(PanelOut));
     L.sigma = take((size_t)(n > 0 ? n : 1) * 4);
     const int64_t nn = n > 0 ? n : 1;
+    L.uinv = take((size_t)nn * 16);
+    L.xblk = take((size_t)2 * TB * TB * 4);
     L.opA = take(tc_operand_bytes(nn, limbs));
     L.opB = L.opA + (size_t)round_up(round_up(nn, 128) * (int64_t)limbs * KP_MAX * 2, 256);
     L.total = off;
@@ -289,32 +461,44 @@ extern "C" int ldlt_rpm_trss_ws(int64_t n, uint32_t p, const uint32_t *U, int64_
     // loop state "running" and an update record with no abort: the SYRDK kernel's liveness test
     if (cudaMemsetAsync(w, 0, Lo.sigma, st) != cudaSuccess) return LDLT_ERR_CUDA;
     trss_iota_kernel<<<(unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), 256, 0, st>>>(sigma, n);
-    for (int64_t k0 = 0; k0 < n; k0 += TB) {
+    uint4 *dq = (uint4 *)(w + Lo.uinv);
+    uint32_t *xblk = (uint32_t *)(w + Lo.xblk);
+    trss_uinv_kernel<<<(unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), 256, 0, st>>>(U, ldu, n, dq,
+                                                                                                  status, f);
+    TrssStep sp;
+    sp.n = n; sp.ldu = ldu; sp.ldc = ldc; sp.U = U; sp.dq = dq; sp.C = C; sp.status = status; sp.f = f;
+    sp.sa = tc_split_args(f, limbs, opA, opB);
+    sp.out = out;
+    sp.xprev = nullptr; sp.kprev = 0; sp.nbprev = 0;
+    const bool big = p >= (1u << 28);
+    for (int64_t k0 = 0, step = 0; k0 < n; k0 += TB, ++step) {
         const int nb = (int)((n - k0) < TB ? (n - k0) : TB);
-        if (p >= (1u << 28)) trss_diag_kernel<true><<<1, TB * TB, 0, st>>>(k0, nb, U, ldu, C, ldc, status, f);
-        else trss_diag_kernel<false><<<1, TB * TB, 0, st>>>(k0, nb, U, ldu, C, ldc, status, f);
         const int64_t k1 = k0 + nb, rest = n - k1;
+        const bool tc = rest >= TRSS_TC_MIN;
+        sp.k0 = k0; sp.nb = nb;
+        sp.xcur = xblk + (step & 1) * TB * TB;
+        // one CTA per TB trailing columns (tensor form: per TB operand rows, padded to 128)
+        const int64_t cols = tc ? round_up(rest, 128) : rest;
+        const unsigned grid = (unsigned)(cols > 0 ? (cols + TB - 1) / TB : 1);
+        if (tc) {
+            if (big) trss_step_kernel<true, true><<<grid, TB * TB, 0, st>>>(sp);
+            else trss_step_kernel<false, true><<<grid, TB * TB, 0, st>>>(sp);
+        } else {
+            if (big) trss_step_kernel<true, false><<<grid, TB * TB, 0, st>>>(sp);
+            else trss_step_kernel<false, false><<<grid, TB * TB, 0, st>>>(sp);
+        }
+        sp.xprev = sp.xcur; sp.kprev = k0; sp.nbprev = nb;
         if (rest <= 0) continue;
-        const unsigned gw = (unsigned)((rest + PW - 1) / PW);
-        if (p >= (1u << 28))
-            trss_panel_kernel<true><<<gw, PW * 32, 0, st>>>(k0, nb, n, U, ldu, C, ldc, f);
-        else
-            trss_panel_kernel<false><<<gw, PW * 32, 0, st>>>(k0, nb, n, U, ldu, C, ldc, f);
-        if (rest >= TRSS_TC_MIN) {
+        if (tc) {
             // C_rr -= X^T U + U^T X on tensor cores: the SYRDK kernel on C's upper triangle
-            if (launch_trss_split_tc(U, ldu, C, ldc, k0, nb, k1, (int)rest, out, f, limbs, opA, opB, st) !=
-                cudaSuccess)
-                return LDLT_ERR_CUDA;
             uint32_t *blk = C + k1 * ldc + k1;
             if (launch_syrdk_tc(blk, ldc, sigma, ls, out, opA, opB, limbs, f, blk, 2000000000LL, status, nsm, 0,
                                 st, 1) != cudaSuccess)
                 return LDLT_ERR_CUDA;
         } else {
             const unsigned gp = (unsigned)((rest + TC - 1) / TC);
-            if (p >= (1u << 28))
-                trss_syr2k_kernel<true><<<dim3(gp, gp), 256, 0, st>>>(k0, nb, n, U, ldu, C, ldc, f);
-            else
-                trss_syr2k_kernel<false><<<dim3(gp, gp), 256, 0, st>>>(k0, nb, n, U, ldu, C, ldc, f);
+            if (big) trss_syr2k_kernel<true><<<dim3(gp, gp), 256, 0, st>>>(k0, nb, n, U, ldu, C, ldc, f);
+            else trss_syr2k_kernel<false><<<dim3(gp, gp), 256, 0, st>>>(k0, nb, n, U, ldu, C, ldc, f);
         }
     }
     return cudaGetLastError() == cudaSuccess ? LDLT_OK : LDLT_ERR_CUDA;
