@@ -760,9 +760,11 @@ def main():
         macs = nt ** 3 / 3.0  # the SYR2K updates dominate: sum over blocks of b (n - k)^2
         trss_line = {"n": nt, "p": pt, "ms": ms_tr, "gmac_per_s": macs / (ms_tr * 1e-3) / 1e9,
                      "status": forms[True][1],
-                     "form": "blocked right-looking (32-row blocks): diagonal TRSS, panel TRMM+TRSM "
-                             "(a warp per column), trailing SYR2K on tcgen05 (bf16 limbs, exact) for "
-                             "orders >= 256, CUDA cores below",
+                     "form": "blocked right-looking (32-row blocks), one launch per block for the "
+                             "diagonal TRSS (X = M U with M from V^T C V, V = U_kk^-1 precomputed), the "
+                             "panel TRMM+TRSM (a warp per column) and the update's limb operands, then "
+                             "the trailing SYR2K on tcgen05 (bf16 limbs, exact) for orders >= 256, "
+                             "CUDA cores below",
                      "cuda_core_form": {"ms": forms[False][0], "status": forms[False][1]},
                      "bit_exact_vs_cuda_core_form": bool(torch.equal(forms[True][2], forms[False][2]))}
         del wst, forms

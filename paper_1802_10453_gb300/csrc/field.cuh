@@ -97,21 +97,6 @@ __device__ __forceinline__ uint32_t fp_sub(uint32_t a, uint32_t b, const FieldP 
 }
 
 // acc += a * b without overflow (see the header comment).
-// Shoup's multiplication by a fixed residue w (V. Shoup, NTL): with the
-// companion wq = floor(w 2^32 / p), q = hi32(x wq) makes x w - q p lie in
-// [0, 2p) for any x < 2^32 (p < 2^31), so 32-bit arithmetic is exact; one
-// correction gives x w mod p.  Pays off when w serves many products.
-__device__ __forceinline__ uint32_t fp_shoup_pre(uint32_t w, const FieldP &f)
-{
-    return (uint32_t)(((uint64_t)w << 32) / (uint64_t)f.p);
-}
-
-__device__ __forceinline__ uint32_t fp_mul_shoup(uint32_t x, uint32_t w, uint32_t wq, const FieldP &f)
-{
-    const uint32_t r = x * w - __umulhi(x, wq) * f.p;
-    return r >= f.p ? r - f.p : r;
-}
-
 __device__ __forceinline__ void fp_mac(uint64_t &acc, uint32_t a, uint32_t b, const FieldP &f)
 {
     acc += (uint64_t)a * (uint64_t)b;

@@ -6,7 +6,8 @@
 // Algorithm 1 halves recursively: X1 from (U1, C1); D2 = C2 - X1^T U2 (TRMM);
 // X2 = U1^{-T} D2 (TRSM); D3 = C3 - (X2^T U2 + U2^T X2) (SYR2K); X3 from
 // (U3, D3).  Unrolled over blocks of TB rows from the top it is the
-// right-looking form run here, three launches per block k (rows [k0, k1)):
+// right-looking form, run here in two forms (block k = rows [k0, k1)).
+// ldlt_rpm_trss (CUDA cores), three launches per block:
 //   trss_diag_kernel   X_kk from U_kk and C_kk: the same steps with blocks of
 //                      one row, in one CTA (x_ii = c_ii / (2 u_ii), the row
 //                      to its right, a rank-2 update of the rest of the block)
@@ -14,6 +15,13 @@
 //                      columns r >= k1, a warp per column
 //   trss_syr2k_kernel  C_r,r -= X_k,r^T U_k,r + U_k,r^T X_k,r on the upper
 //                      triangle of the trailing block, 64 x 64 tiles
+// ldlt_rpm_trss_ws (tensor cores), the inverses V_k = U_kk^{-1} of all
+// diagonal blocks once (trss_vinv_kernel), then two launches per block:
+//   trss_step_kernel   X_kk by dense products with V_k (no substitution
+//                      chain), the panel X_k,r = V_k^T (C_k,r - X_kk^T U_k,r),
+//                      and the trailing update's limb operands
+//   syrdk_tc_kernel    the SYR2K on tcgen05 (upper-triangle mode) for
+//                      trailing orders >= 256; trss_syr2k_kernel below
 // Characteristic 2: the diagonal of X^T U + U^T X is zero, so a solution
 // exists only if C's diagonal (after the updates) is zero; x_ii = 0 is taken
 // and a non-zero diagonal entry is reported as LDLT_ERR_INCONSISTENT.
@@ -213,42 +221,73 @@ __global__ void __launch_bounds__(256) trss_syr2k_kernel(int64_t k0, int nb, int
         }
 }
 
-// Per diagonal entry of U, once per call (every block step reads them):
-// 1 / u_ii and h_i = 1 / (2 u_ii) (0 for p = 2), each with its Shoup
-// companion, at dq[4 i .. 4 i + 3] = {1/u_ii, companion, h_i, companion}.  A
-// zero diagonal entry is reported as LDLT_ERR_ARG.
-__global__ void trss_uinv_kernel(const uint32_t *U, int64_t ldu, int64_t n, uint4 *dq, int32_t *status, FieldP f)
+// 64-bit sum of products a b of residues: exact for p < 2^28 over up to 64
+// products (each < 2^56); larger p fold after every product.
+template <bool BIG>
+__device__ __forceinline__ void mac2(uint64_t &acc, uint32_t a, uint32_t b, const FieldP &f)
 {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t d = rd(U, ldu, i, i, f);
-        if (d == 0u) atomicCAS(status, 0, LDLT_ERR_ARG);
-        const uint32_t ui = d ? fp_inv(d, f) : 0u;
-        const uint32_t h = fp_mul(ui, f.inv2, f);
-        dq[i] = make_uint4(ui, fp_shoup_pre(ui, f), h, fp_shoup_pre(h, f));
-    }
+    if (BIG) fp_mac(acc, a, b, f);
+    else acc += (uint64_t)a * (uint64_t)b;
 }
 
-// One block step of the tensor-core form in one launch: every CTA solves the
-// diagonal block X_kk (the same nb-step substitution as trss_diag_kernel, in
-// shared memory; the CTAs agree bit for bit), then each of its TB warps
-// solves one column j >= k1 of the panel X_k,r as trss_panel_kernel does, and
-// (SPLIT) the CTA writes its TB rows i = j - k1 of the trailing update's limb
-// operands, G[i] = [X_k,i | U_k,i] and GD[i] = [U_k,i | X_k,i], so that
-// GD G^T = U^T X + X^T U (rows past the last column are the zero rows that
-// pad the operands to 128).  C_kk is read by every CTA, so X_kk is not
+// V_k = U_kk^{-1} for every diagonal block of U (upper triangular, TB x TB,
+// row-major at V + k TB^2), once per call: U is not changed by the solve.
+// One warp per block, lane i computes row i of V from V U = I:
+//   v_ii = 1 / u_ii,   v_il = -(sum_{i <= k < l} v_ik u_kl) / u_ll  (l > i).
+// A zero diagonal entry of U is reported as LDLT_ERR_ARG.
+template <bool BIG>
+__global__ void __launch_bounds__(32) trss_vinv_kernel(const uint32_t *U, int64_t ldu, int64_t n, uint32_t *V,
+                                                      int32_t *status, FieldP f)
+{
+    __shared__ uint32_t u[TB][TB + 1], v[TB][TB + 1];
+    const int lane = threadIdx.x;
+    const int64_t k0 = (int64_t)blockIdx.x * TB;
+    const int nb = (int)(n - k0 < TB ? n - k0 : TB);
+    for (int r = 0; r < TB; ++r) {
+        u[r][lane] = (r < nb && lane < nb && r <= lane) ? rd(U, ldu, k0 + r, k0 + lane, f) : 0u;
+        v[r][lane] = 0u;
+    }
+    __syncwarp();
+    const uint32_t d = lane < nb ? u[lane][lane] : 1u;
+    if (d == 0u) atomicCAS(status, 0, LDLT_ERR_ARG);
+    const uint32_t ui = d ? fp_inv(d, f) : 0u;
+    if (lane < nb) v[lane][lane] = ui;
+    for (int l = 1; l < nb; ++l) {
+        const uint32_t ul = __shfl_sync(0xffffffffu, ui, l);
+        if (lane < l) {
+            uint64_t acc = 0;
+            for (int k = lane; k < l; ++k) mac2<BIG>(acc, v[lane][k], u[k][l], f);
+            const uint32_t sl = fp_reduce64_fold(acc, f);
+            v[lane][l] = fp_mul(sl ? f.p - sl : 0u, ul, f);
+        }
+    }
+    __syncwarp();
+    uint32_t *Vk = V + (int64_t)blockIdx.x * TB * TB;
+    for (int r = 0; r < TB; ++r) Vk[r * TB + lane] = v[r][lane];
+}
+
+// One block step of the tensor-core form in one launch.  With V = U_kk^{-1}
+// (precomputed) the diagonal problem X^T U + U^T X = C_kk is solved without
+// a sequential substitution: M = X V is upper triangular and
+// M + M^T = V^T C_kk V =: S, so M takes S's strict upper triangle and half
+// its diagonal (characteristic 2: a zero diagonal, and S_ii != 0 means the
+// system has no solution) and X_kk = M U_kk -- three dense TB x TB products.
+// Each of the CTA's TB warps then solves one column j >= k1 of the panel,
+// X_k,j = V^T (C_k,j - X_kk^T U_k,j) (two products by triangular matrices,
+// a lane per block row), and (SPLIT) the CTA writes its TB rows
+// i = j - k1 of the trailing update's limb operands, G[i] = [X_k,i | U_k,i]
+// and GD[i] = [U_k,i | X_k,i], so that GD G^T = U^T X + X^T U (rows past the
+// last column are the zero rows that pad the operands to 128).  The solution
+// is unique (for p = 2 once x_ii = 0), so it equals the one Algorithm 1's
+// recursion computes, bit for bit.  C_kk is read by every CTA, so X_kk is not
 // written back here: CTA 0 keeps it in xcur and the next step's CTA 0 (which
 // does not read block k) stores it into C; a launch with no trailing columns
 // (the last block, one CTA) stores its own.
-//
-// The dependent chain of a substitution step uses products by residues that
-// are fixed for the step (1/u_ii, 1/(2 u_ii), u_il / u_ii), so they are
-// Shoup products with precomputed companions: x_ii = c_ii h_i and
-// x_il = c_il / u_ii - x_ii (u_il / u_ii), two products on the chain.
 struct TrssStep {
     int64_t k0, n, ldu, ldc;
     int nb;
     const uint32_t *U;
-    const uint4 *dq;        // per diagonal entry: 1/u_ii, h_i and companions
+    const uint32_t *V;      // U_kk^{-1} of every diagonal block
     uint32_t *C;
     int32_t *status;
     FieldP f;
@@ -263,9 +302,8 @@ struct TrssStep {
 template <bool BIG, bool SPLIT>
 __global__ void __launch_bounds__(TB * TB) trss_step_kernel(const TrssStep s)
 {
-    __shared__ uint32_t u[TB][TB + 1], x[TB][TB + 1], v[TB][TB + 1], vq[TB][TB + 1];
+    __shared__ uint32_t u[TB][TB + 1], vv[TB][TB + 1], c[TB][TB + 1], t1[TB][TB + 1], x[TB][TB + 1];
     __shared__ uint32_t ys[TB][TB + 1], us[TB][TB + 1];
-    __shared__ uint4 dq[TB];
     const FieldP f = s.f;
     const int nb = s.nb;
     const int64_t k0 = s.k0, k1 = k0 + nb, rest = s.n - k1;
@@ -273,49 +311,34 @@ __global__ void __launch_bounds__(TB * TB) trss_step_kernel(const TrssStep s)
     if (blockIdx.x == 0 && s.xprev && r < s.nbprev && l < s.nbprev && r <= l)
         s.C[(s.kprev + r) * s.ldc + s.kprev + l] = s.xprev[r * TB + l];
     const bool in = r < nb && l < nb && r <= l;
-    const uint32_t url = in ? rd(s.U, s.ldu, k0 + r, k0 + l, f) : 0u;
-    const uint32_t crl = in ? rd(s.C, s.ldc, k0 + r, k0 + l, f) : 0u;
-    const uint4 dr = r < nb ? s.dq[k0 + r] : make_uint4(0, 0, 0, 0);
-    u[r][l] = url;
-    x[r][l] = 0u;
-    {
-        const uint32_t vr = fp_mul(url, dr.x, f);  // u_rl / u_rr
-        v[r][l] = vr;
-        vq[r][l] = fp_shoup_pre(vr, f);
-    }
-    if (l == 0) dq[r] = dr;
+    const bool sq = r < nb && l < nb;
+    u[r][l] = in ? rd(s.U, s.ldu, k0 + r, k0 + l, f) : 0u;
+    vv[r][l] = s.V[(k0 / TB) * TB * TB + r * TB + l];  // zero outside the upper nb x nb triangle
+    c[r][l] = sq ? rd(s.C, s.ldc, k0 + (r < l ? r : l), k0 + (r < l ? l : r), f) : 0u;  // C_kk is symmetric
     __syncthreads();
-    // ---- X_kk ----
-    uint64_t acc = 0;
-    for (int i = 0; i < nb; ++i) {
-        if (r == i) {
-            const uint32_t ci = fp_sub(crl, fp_reduce64_fold(acc, f), f);  // c_il after steps < i
-            uint32_t xii = 0;
-            if (l == i) {
-                if (f.p == 2u) {
-                    if (ci != 0u && blockIdx.x == 0) atomicCAS(s.status, 0, LDLT_ERR_INCONSISTENT);
-                } else {
-                    xii = fp_mul_shoup(ci, dr.z, dr.w, f);
-                }
-            }
-            const uint32_t ciu = fp_mul_shoup(ci, dr.x, dr.y, f);  // off the chain of x_ii
-            xii = __shfl_sync(0xffffffffu, xii, i);
-            uint32_t xil = 0;
-            if (l == i) xil = xii;
-            else if (l > i && l < nb) xil = fp_sub(ciu, fp_mul_shoup(xii, v[i][l], vq[i][l], f), f);
-            x[i][l] = xil;
-        }
-        // rows < i are final: their warps have left, warps i .. TB-1 meet
-        asm volatile("bar.sync 1, %0;" ::"r"((TB - i) * 32) : "memory");
-        if (r == i) break;  // row i is done
-        if (r <= l && l < nb) {
-            if (BIG) {
-                fp_mac(acc, x[i][r], u[i][l], f);
-                fp_mac(acc, u[i][r], x[i][l], f);
-            } else {
-                acc += (uint64_t)x[i][r] * u[i][l] + (uint64_t)u[i][r] * x[i][l];
-            }
-        }
+    // ---- X_kk: T1 = C V, S = V^T T1, M from S, X = M U ----
+    {
+        uint64_t acc = 0;
+        for (int k = 0; k <= l; ++k) mac2<BIG>(acc, c[r][k], vv[k][l], f);
+        t1[r][l] = fp_reduce64_fold(acc, f);
+    }
+    __syncthreads();
+    uint32_t mrl = 0;
+    if (r <= l) {
+        uint64_t acc = 0;
+        for (int k = 0; k <= r; ++k) mac2<BIG>(acc, vv[k][r], t1[k][l], f);
+        const uint32_t srl = fp_reduce64_fold(acc, f);
+        if (r < l) mrl = srl;
+        else if (f.p != 2u) mrl = fp_mul(srl, f.inv2, f);
+        else if (srl != 0u && r < nb && blockIdx.x == 0) atomicCAS(s.status, 0, LDLT_ERR_INCONSISTENT);
+    }
+    __syncthreads();
+    c[r][l] = mrl;  // M (C_kk is no longer needed)
+    __syncthreads();
+    {
+        uint64_t acc = 0;
+        for (int k = r; k <= l; ++k) mac2<BIG>(acc, c[r][k], u[k][l], f);
+        x[r][l] = r <= l ? fp_reduce64_fold(acc, f) : 0u;
     }
     __syncthreads();
     if (blockIdx.x == 0 && in) {
@@ -331,25 +354,18 @@ __global__ void __launch_bounds__(TB * TB) trss_step_kernel(const TrssStep s)
         const bool row = lane < nb;
         ucj = row ? rd(s.U, s.ldu, k0 + lane, j, f) : 0u;
         const uint32_t ccj = row ? rd(s.C, s.ldc, k0 + lane, j, f) : 0u;
-        uint64_t a2 = 0;
+        uint64_t acc = 0;
         for (int k = 0; k < nb; ++k) {  // sum_{k <= lane} x_k,lane u_kj (x is upper triangular)
             const uint32_t ukj = __shfl_sync(0xffffffffu, ucj, k);
-            if (BIG) fp_mac(a2, x[k][lane], ukj, f);
-            else a2 += (uint64_t)x[k][lane] * ukj;
+            mac2<BIG>(acc, x[k][lane], ukj, f);
         }
-        const uint4 dl = dq[lane];
-        for (int q = 0; q < nb; ++q) {
-            uint32_t yq = 0;
-            if (lane == q) {
-                yq = fp_mul_shoup(fp_sub(ccj, fp_reduce64_fold(a2, f), f), dl.x, dl.y, f);
-                y = yq;
-            }
-            yq = __shfl_sync(0xffffffffu, yq, q);
-            if (lane > q) {
-                if (BIG) fp_mac(a2, u[q][lane], yq, f);
-                else a2 += (uint64_t)u[q][lane] * yq;
-            }
+        const uint32_t t = fp_sub(ccj, fp_reduce64_fold(acc, f), f);
+        acc = 0;
+        for (int k = 0; k < nb; ++k) {  // y = V^T t
+            const uint32_t tk = __shfl_sync(0xffffffffu, t, k);
+            mac2<BIG>(acc, vv[k][lane], tk, f);
         }
+        y = row ? fp_reduce64_fold(acc, f) : 0u;
         if (row) s.C[(k0 + lane) * s.ldc + j] = y;
     }
     if (SPLIT) {
@@ -409,7 +425,7 @@ void trss_layout(int64_t n, uint32_t p, TrssLayout &L)
     L.out = take(sizeof(PanelOut));
     L.sigma = take((size_t)(n > 0 ? n : 1) * 4);
     const int64_t nn = n > 0 ? n : 1;
-    L.uinv = take((size_t)nn * 16);
+    L.uinv = take((size_t)round_up(nn, TB) * TB * 4);  // U_kk^{-1} of every diagonal block
     L.xblk = take((size_t)2 * TB * TB * 4);
     L.opA = take(tc_operand_bytes(nn, limbs));
     L.opB = L.opA + (size_t)round_up(round_up(nn, 128) * (int64_t)limbs * KP_MAX * 2, 256);
@@ -461,16 +477,17 @@ extern "C" int ldlt_rpm_trss_ws(int64_t n, uint32_t p, const uint32_t *U, int64_
     // loop state "running" and an update record with no abort: the SYRDK kernel's liveness test
     if (cudaMemsetAsync(w, 0, Lo.sigma, st) != cudaSuccess) return LDLT_ERR_CUDA;
     trss_iota_kernel<<<(unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), 256, 0, st>>>(sigma, n);
-    uint4 *dq = (uint4 *)(w + Lo.uinv);
+    uint32_t *V = (uint32_t *)(w + Lo.uinv);
     uint32_t *xblk = (uint32_t *)(w + Lo.xblk);
-    trss_uinv_kernel<<<(unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), 256, 0, st>>>(U, ldu, n, dq,
-                                                                                                  status, f);
+    const bool big = p >= (1u << 28);
+    const unsigned nblk = (unsigned)((n + TB - 1) / TB);
+    if (big) trss_vinv_kernel<true><<<nblk, 32, 0, st>>>(U, ldu, n, V, status, f);
+    else trss_vinv_kernel<false><<<nblk, 32, 0, st>>>(U, ldu, n, V, status, f);
     TrssStep sp;
-    sp.n = n; sp.ldu = ldu; sp.ldc = ldc; sp.U = U; sp.dq = dq; sp.C = C; sp.status = status; sp.f = f;
+    sp.n = n; sp.ldu = ldu; sp.ldc = ldc; sp.U = U; sp.V = V; sp.C = C; sp.status = status; sp.f = f;
     sp.sa = tc_split_args(f, limbs, opA, opB);
     sp.out = out;
     sp.xprev = nullptr; sp.kprev = 0; sp.nbprev = 0;
-    const bool big = p >= (1u << 28);
     for (int64_t k0 = 0, step = 0; k0 < n; k0 += TB, ++step) {
         const int nb = (int)((n - k0) < TB ? (n - k0) : TB);
         const int64_t k1 = k0 + nb, rest = n - k1;
