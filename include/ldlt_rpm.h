@@ -459,7 +459,10 @@ int ldlt_rpm_profile_read(double out[32]);
  *               lower triangle of the m' remaining rows read and the new one
  *               written, 8 m'(m'+1)/2, plus the operands once (as above)
  *   out[13]     level-3 update launches
- *   out[14..15] reserved (0)
+ *   out[14]     the part of out[12] that falls on the first three update
+ *               launches of each call (the largest: what a traffic capture
+ *               of three launches measures)
+ *   out[15]     reserved (0)
  * Returns LDLT_OK, or LDLT_ERR_ARG for a NULL pointer.
  */
 int ldlt_rpm_profile_read_hbm(double out[16]);

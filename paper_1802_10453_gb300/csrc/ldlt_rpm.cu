@@ -396,6 +396,7 @@ int run_profiled(const Plan &c, cudaStream_t st)
     hb[4] += 1;
     hb[8] += 8.0 * tri;  // lower triangle of A read, of S written
     int m = (int)c.n;
+    int nupd = 0;  // update launches of this call
     int lb = 0, la = 0, ash = 8;
     if (c.path == LDLT_PATH_TC) { lb = c.limbs; la = tc_limbs_a(c.p, &ash); }
     for (int ipanel = 0;; ++ipanel) {
@@ -431,6 +432,7 @@ int run_profiled(const Plan &c, cudaStream_t st)
                 // the update: the old lower triangle read and the new one written, the operands read once
                 hb[12] += 8.0 * (double)m_next * (double)(m_next + 1) * 0.5 + ops;
                 hb[13] += 1;
+                if (nupd++ < 3) hb[14] += 8.0 * (double)m_next * (double)(m_next + 1) * 0.5 + ops;
             }
         }
         m = m_next;

@@ -10,7 +10,8 @@ in 2x2 pairs, p = 2^26 - 5 unless given) on the GPU; the second draws the named
 workload of inputs.WORKLOADS exactly as bench.py does; both factor it once
 through the C ABI, as one CUDA graph, or with `host` from the profiling host
 loop (the same kernels launched one by one from the host, one readback per
-panel), which is what the ncu captures of single kernels use.  The third draws the first COUNT matrices of the batch
+panel), which is what the ncu captures of single kernels use; it also prints
+the algorithmic bytes of the level-3 update launches.  The third draws the first COUNT matrices of the batch
 workload (n in [32, 512], p = 65521) and factors them in one batched call.
 The fourth solves one TRSS (Algorithm 1) of order N (random upper triangular
 U with a non-zero diagonal, random symmetric C; p = 8388593 unless given).
@@ -62,12 +63,21 @@ def main(argv):
         r = n // 2
         A, _ = inputs_gpu.planted_matrix(n, r, r // 4, p, 12345)
     if host:
+        lr.lib().ldlt_rpm_profile_reset()
         lr.lib().ldlt_rpm_profile_enable(1)
     res = lr.factor(A, p, path=path)
     torch.cuda.synchronize()
     if host:
         lr.lib().ldlt_rpm_profile_enable(0)
     print("n", n, "p", p, "rank", int(res["rank"].item()), "status", int(res["status"].item()))
+    if host:
+        import ctypes
+        hb = (ctypes.c_double * 16)()
+        lr.lib().ldlt_rpm_profile_read_hbm(hb)
+        # the level-3 updates' algorithmic bytes (old lower triangle read, new
+        # one written, operands once) and their launches, for the ncu traffic ratio
+        print("update_alg_bytes %.6e update_launches %d first_three_alg_bytes %.6e"
+              % (hb[12], int(hb[13]), hb[14]))
     return 0
 
 
