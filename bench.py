@@ -765,7 +765,7 @@ def main():
         macs = nt ** 3 / 3.0  # the SYR2K updates dominate: sum over blocks of b (n - k)^2
         trss_line = {"n": nt, "p": pt, "ms": ms_tr, "gmac_per_s": macs / (ms_tr * 1e-3) / 1e9,
                      "status": forms[True][1],
-                     "form": "blocked right-looking (32-row blocks), one launch per block for the "
+                     "form": "blocked right-looking (64-row blocks), one launch per block for the "
                              "diagonal TRSS (X = M U with M from V^T C V, V = U_kk^-1 precomputed), the "
                              "panel TRMM+TRSM (a warp per column) and the update's limb operands, then "
                              "the trailing SYR2K on tcgen05 (bf16 limbs, exact) for orders >= 256, "

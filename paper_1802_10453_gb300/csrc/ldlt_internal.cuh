@@ -188,12 +188,6 @@ cudaError_t launch_syrdk_tc(const uint32_t *S, int64_t ldS, const int *sigma, co
                             const PanelOut *out, const void *Aop, const void *Bop, int limbs,
                             FieldP f, uint32_t *Snext, int64_t budget_ns, int32_t *status,
                             int num_sms, int test_drop, cudaStream_t st, int upper = 0);
-// Limb operands of TRSS's trailing update (Algorithm 1's SYR2K) for block rows
-// k0 .. k0+nb-1 and the m trailing columns from r0; also writes the sizes the
-// SYRDK kernel reads from out.
-cudaError_t launch_trss_split_tc(const uint32_t *U, int64_t ldu, const uint32_t *X, int64_t ldx, int64_t k0, int nb,
-                                 int64_t r0, int m, PanelOut *out, FieldP f, int limbs, void *Aop, void *Bop,
-                                 cudaStream_t st);
 
 // A panel step is live while the loop has not ended and its panel did not
 // abort; the kernels after the panel do nothing otherwise.

@@ -537,46 +537,6 @@ __global__ void split_tc_kernel(const SplitArgs a)
     split_write(a, i, k0, kpad, kprime, rows, gd_bal, gk);
 }
 
-// Operands of Algorithm 1's trailing update C_rr -= X_k,r^T U_k,r + U_k,r^T X_k,r
-// (the SYR2K of TRSS) in the SYRDK layout: for trailing row i the K = 2 nb
-// entries G[i] = [X_k,i | U_k,i] and GD[i] = [U_k,i | X_k,i] (block rows
-// k0 .. k0+nb-1, column r0 + i), so GD G^T = U^T X + X^T U.  Thread (0, 0) of
-// the grid writes the update's sizes for the SYRDK kernel.
-__global__ void trss_split_tc_kernel(const SplitArgs a, const uint32_t *__restrict__ U, int64_t ldu,
-                                     const uint32_t *__restrict__ X, int64_t ldx, int64_t k0, int nb, int64_t r0,
-                                     int m, PanelOut *out)
-{
-    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
-        out->m_next = m;
-        out->np = 2 * nb;
-        out->abort = 0;
-    }
-    const int np = 2 * nb;
-    const int kpad = (np + 63) / 64 * 64, rows = (m + BM - 1) / BM * BM, kprime = a.la * kpad;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int k0g = blockIdx.y * 8;
-    if (i >= rows || k0g >= kpad) return;
-    const FieldP f = a.f;
-    uint32_t gk[8];
-    int32_t gd_bal[8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-        const int k = k0g + e;
-        uint32_t gv = 0, dv = 0;
-        if (i < m && k < np) {
-            const int kk = k < nb ? k : k - nb;
-            uint32_t xu = U[(k0 + kk) * ldu + r0 + i];
-            if (xu >= f.p) xu %= f.p;
-            const uint32_t xx = X[(k0 + kk) * ldx + r0 + i];  // X_k,r: already reduced
-            gv = k < nb ? xx : xu;
-            dv = k < nb ? xu : xx;
-        }
-        gk[e] = gv;
-        gd_bal[e] = balanced(dv, f.p);
-    }
-    split_write(a, i, k0g, kpad, kprime, rows, gd_bal, gk);
-}
-
 }  // namespace
 
 // Number of signed 8-bit digits so that every balanced residue |x| <= (p-1)/2
@@ -675,30 +635,6 @@ SplitArgs tc_split_args(FieldP f, int limbs, void *Aop, void *Bop)
     return a;
 }
 
-cudaError_t launch_trss_split_tc(const uint32_t *U, int64_t ldu, const uint32_t *X, int64_t ldx, int64_t k0, int nb,
-                                 int64_t r0, int m, PanelOut *out, FieldP f, int limbs, void *Aop, void *Bop,
-                                 cudaStream_t st)
-{
-    if (m <= 0) return cudaSuccess;
-    SplitArgs a;
-    a.LpC = nullptr; a.ldL = 0; a.sigma = nullptr;
-    int ash = 8;
-    a.lb = limbs; a.la = tc_limbs_a(f.p, &ash); a.ash = ash; a.bn = tc_bn(limbs);
-    a.nprime = limbs * a.bn;
-    a.ls = nullptr; a.out = out; a.f = f;
-    a.S = nullptr; a.ldS = 0; a.Snext = nullptr;
-    uint64_t w = 1;
-    for (int u = 0; u < 4; ++u) {
-        a.wbase[u] = (uint32_t)(w % f.p);
-        w = (w << ash) % f.p;
-    }
-    a.Aop = (__nv_bfloat16 *)Aop;
-    a.Bop = (__nv_bfloat16 *)Bop;
-    const int kpad = (2 * nb + 63) / 64 * 64;
-    dim3 grid((unsigned)((round_up(m, BM) + 127) / 128), (unsigned)(kpad / 8));
-    trss_split_tc_kernel<<<grid, 128, 0, st>>>(a, U, ldu, X, ldx, k0, nb, r0, m, out);
-    return cudaGetLastError();
-}
 
 cudaError_t launch_syrdk_tc(const uint32_t *S, int64_t ldS, const int *sigma, const LoopState *ls,
                             const PanelOut *out, const void *Aop, const void *Bop, int limbs, FieldP f,

@@ -15,8 +15,9 @@
 //                      columns r >= k1, a warp per column
 //   trss_syr2k_kernel  C_r,r -= X_k,r^T U_k,r + U_k,r^T X_k,r on the upper
 //                      triangle of the trailing block, 64 x 64 tiles
-// ldlt_rpm_trss_ws (tensor cores), the inverses V_k = U_kk^{-1} of all
-// diagonal blocks once (trss_vinv_kernel), then two launches per block:
+// ldlt_rpm_trss_ws (tensor cores), blocks of TW = 64 rows: the inverses
+// V_k = U_kk^{-1} of all diagonal blocks once (trss_vinv_kernel), then two
+// launches per block:
 //   trss_step_kernel   X_kk by dense products with V_k (no substitution
 //                      chain), the panel X_k,r = V_k^T (C_k,r - X_kk^T U_k,r),
 //                      and the trailing update's limb operands
@@ -158,15 +159,17 @@ __global__ void __launch_bounds__(PW * 32) trss_panel_kernel(int64_t k0, int nb,
     if (row) C[(k0 + lane) * ldc + j] = y;
 }
 
-// C[i][j] -= sum_k (X[k][i] U[k][j] + U[k][i] X[k][j]) for k in the block,
-// k1 <= i <= j < n; one 64 x 64 tile per CTA, 4 x 4 outputs per thread.  For
-// p < 2^28 the 2 TB products of a block (each < 2^56) sum below 2^63 without
-// folding; larger p fold after every product.
+// C[i][j] -= sum_k (X[k][i] U[k][j] + U[k][i] X[k][j]) for the nb <= TB rows
+// k of block rows k0 .. k0+nb-1, k1 <= i <= j < n (k1 >= k0 + nb: the first
+// trailing index, which a 64-row block updates in two 32-row halves); one
+// 64 x 64 tile per CTA, 4 x 4 outputs per thread.  For p < 2^28 the 2 TB
+// products (each < 2^56) sum below 2^63 without folding; larger p fold after
+// every product.
 template <bool BIG>
-__global__ void __launch_bounds__(256) trss_syr2k_kernel(int64_t k0, int nb, int64_t n, const uint32_t *U,
-                                                          int64_t ldu, uint32_t *C, int64_t ldc, FieldP f)
+__global__ void __launch_bounds__(256) trss_syr2k_kernel(int64_t k0, int nb, int64_t k1, int64_t n,
+                                                          const uint32_t *U, int64_t ldu, uint32_t *C, int64_t ldc,
+                                                          FieldP f)
 {
-    const int64_t k1 = k0 + nb;
     const int bi = blockIdx.y, bj = blockIdx.x;
     if (bi > bj) return;  // tiles wholly below the diagonal
     const int64_t i0 = k1 + (int64_t)bi * TC, j0 = k1 + (int64_t)bj * TC;
@@ -230,59 +233,76 @@ __device__ __forceinline__ void mac2(uint64_t &acc, uint32_t a, uint32_t b, cons
     else acc += (uint64_t)a * (uint64_t)b;
 }
 
-// V_k = U_kk^{-1} for every diagonal block of U (upper triangular, TB x TB,
-// row-major at V + k TB^2), once per call: U is not changed by the solve.
-// One warp per block, lane i computes row i of V from V U = I:
+// V_k = U_kk^{-1} for every TW-row diagonal block of U (upper triangular,
+// TW x TW, row-major at V + k TW^2), once per call: U is not changed by the
+// solve.  One warp per block, lane i computes rows i and i + 32 of V from
+// V U = I:
 //   v_ii = 1 / u_ii,   v_il = -(sum_{i <= k < l} v_ik u_kl) / u_ll  (l > i).
-// A zero diagonal entry of U is reported as LDLT_ERR_ARG.
+// A zero diagonal entry of U is reported as LDLT_ERR_ARG.  For p < 2^28 the
+// sums of at most TW - 1 products (each < 2^56) stay below 2^62.
+constexpr int TW = 64;  // rows per block step of the tensor-core form
+constexpr int TWP = TW + 1;
 template <bool BIG>
 __global__ void __launch_bounds__(32) trss_vinv_kernel(const uint32_t *U, int64_t ldu, int64_t n, uint32_t *V,
                                                       int32_t *status, FieldP f)
 {
-    __shared__ uint32_t u[TB][TB + 1], v[TB][TB + 1];
+    __shared__ uint32_t u[TW][TWP], v[TW][TWP];
     const int lane = threadIdx.x;
-    const int64_t k0 = (int64_t)blockIdx.x * TB;
-    const int nb = (int)(n - k0 < TB ? n - k0 : TB);
-    for (int r = 0; r < TB; ++r) {
-        u[r][lane] = (r < nb && lane < nb && r <= lane) ? rd(U, ldu, k0 + r, k0 + lane, f) : 0u;
-        v[r][lane] = 0u;
-    }
+    const int64_t k0 = (int64_t)blockIdx.x * TW;
+    const int nb = (int)(n - k0 < TW ? n - k0 : TW);
+    for (int r = 0; r < TW; ++r)
+        for (int c = lane; c < TW; c += 32) {
+            u[r][c] = (r < nb && c < nb && r <= c) ? rd(U, ldu, k0 + r, k0 + c, f) : 0u;
+            v[r][c] = 0u;
+        }
     __syncwarp();
-    const uint32_t d = lane < nb ? u[lane][lane] : 1u;
-    if (d == 0u) atomicCAS(status, 0, LDLT_ERR_ARG);
-    const uint32_t ui = d ? fp_inv(d, f) : 0u;
-    if (lane < nb) v[lane][lane] = ui;
+    uint32_t ui[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int i = lane + 32 * h;
+        const uint32_t d = i < nb ? u[i][i] : 1u;
+        if (d == 0u) atomicCAS(status, 0, LDLT_ERR_ARG);
+        ui[h] = d ? fp_inv(d, f) : 0u;
+        if (i < nb) v[i][i] = ui[h];
+    }
     for (int l = 1; l < nb; ++l) {
-        const uint32_t ul = __shfl_sync(0xffffffffu, ui, l);
-        if (lane < l) {
-            uint64_t acc = 0;
-            for (int k = lane; k < l; ++k) mac2<BIG>(acc, v[lane][k], u[k][l], f);
-            const uint32_t sl = fp_reduce64_fold(acc, f);
-            v[lane][l] = fp_mul(sl ? f.p - sl : 0u, ul, f);
+        const uint32_t ul = __shfl_sync(0xffffffffu, l < 32 ? ui[0] : ui[1], l & 31);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int i = lane + 32 * h;
+            if (i < l) {
+                uint64_t acc = 0;
+                for (int k = i; k < l; ++k) mac2<BIG>(acc, v[i][k], u[k][l], f);
+                const uint32_t sl = fp_reduce64_fold(acc, f);
+                v[i][l] = fp_mul(sl ? f.p - sl : 0u, ul, f);
+            }
         }
     }
     __syncwarp();
-    uint32_t *Vk = V + (int64_t)blockIdx.x * TB * TB;
-    for (int r = 0; r < TB; ++r) Vk[r * TB + lane] = v[r][lane];
+    uint32_t *Vk = V + (int64_t)blockIdx.x * TW * TW;
+    for (int r = 0; r < TW; ++r)
+        for (int c = lane; c < TW; c += 32) Vk[r * TW + c] = v[r][c];
 }
 
-// One block step of the tensor-core form in one launch.  With V = U_kk^{-1}
-// (precomputed) the diagonal problem X^T U + U^T X = C_kk is solved without
-// a sequential substitution: M = X V is upper triangular and
-// M + M^T = V^T C_kk V =: S, so M takes S's strict upper triangle and half
-// its diagonal (characteristic 2: a zero diagonal, and S_ii != 0 means the
-// system has no solution) and X_kk = M U_kk -- three dense TB x TB products.
-// Each of the CTA's TB warps then solves one column j >= k1 of the panel,
-// X_k,j = V^T (C_k,j - X_kk^T U_k,j) (two products by triangular matrices,
-// a lane per block row), and (SPLIT) the CTA writes its TB rows
-// i = j - k1 of the trailing update's limb operands, G[i] = [X_k,i | U_k,i]
-// and GD[i] = [U_k,i | X_k,i], so that GD G^T = U^T X + X^T U (rows past the
-// last column are the zero rows that pad the operands to 128).  The solution
-// is unique (for p = 2 once x_ii = 0), so it equals the one Algorithm 1's
-// recursion computes, bit for bit.  C_kk is read by every CTA, so X_kk is not
-// written back here: CTA 0 keeps it in xcur and the next step's CTA 0 (which
-// does not read block k) stores it into C; a launch with no trailing columns
-// (the last block, one CTA) stores its own.
+// One block step of the tensor-core form in one launch (block k = TW rows
+// from k0).  With V = U_kk^{-1} (precomputed) the diagonal problem
+// X^T U + U^T X = C_kk is solved without a sequential substitution: M = X V
+// is upper triangular and M + M^T = V^T C_kk V =: S, so M takes S's strict
+// upper triangle and half its diagonal (characteristic 2: a zero diagonal,
+// and S_ii != 0 means the system has no solution) and X_kk = M U_kk -- three
+// dense TW x TW products.  Each of the CTA's 32 warps then solves one column
+// j >= k1 of the panel, X_k,j = V^T (C_k,j - X_kk^T U_k,j) (two products by
+// triangular matrices, a lane per two block rows), and (SPLIT) the CTA writes
+// its 32 rows i = j - k1 of the trailing update's limb operands,
+// G[i] = [X_k,i | U_k,i] and GD[i] = [U_k,i | X_k,i], so that
+// GD G^T = U^T X + X^T U (K = 2 TW = 128; rows past the last column are the
+// zero rows that pad the operands to 128).  The solution is unique (for
+// p = 2 once x_ii = 0), so it equals the one Algorithm 1's recursion
+// computes, bit for bit.  C_kk is read by every CTA, so X_kk is not written
+// back here: CTA 0 keeps it in xcur and the next step's CTA 0 (which does not
+// read block k) stores it into C; a launch with no trailing columns (the last
+// block, one CTA) stores its own.  Thread t computes the outputs (t / 16,
+// t mod 16 + 16 q), q < 4, of each TW x TW product.
 struct TrssStep {
     int64_t k0, n, ldu, ldc;
     int nb;
@@ -291,7 +311,7 @@ struct TrssStep {
     uint32_t *C;
     int32_t *status;
     FieldP f;
-    const uint32_t *xprev;  // X of the previous block (TB x TB, row-major), or null
+    const uint32_t *xprev;  // X of the previous block (TW x TW, row-major), or null
     int64_t kprev;
     int nbprev;
     uint32_t *xcur;         // this block's X for the next step
@@ -299,92 +319,148 @@ struct TrssStep {
     PanelOut *out;          // SPLIT: the update record the SYRDK kernel reads
 };
 
+constexpr int STEP_THREADS = 1024;
+constexpr size_t STEP_SMEM = (size_t)(4 * TW * TWP + 2 * 32 * TWP) * 4;  // u, V, C/M, T1/X; ys, us
+
 template <bool BIG, bool SPLIT>
-__global__ void __launch_bounds__(TB * TB) trss_step_kernel(const TrssStep s)
+__global__ void __launch_bounds__(STEP_THREADS) trss_step_kernel(const TrssStep s)
 {
-    __shared__ uint32_t u[TB][TB + 1], vv[TB][TB + 1], c[TB][TB + 1], t1[TB][TB + 1], x[TB][TB + 1];
-    __shared__ uint32_t ys[TB][TB + 1], us[TB][TB + 1];
+    extern __shared__ uint32_t sm[];
+    uint32_t(*u)[TWP] = reinterpret_cast<uint32_t(*)[TWP]>(sm);
+    uint32_t(*vv)[TWP] = u + TW;
+    uint32_t(*c)[TWP] = vv + TW;   // C_kk, then M
+    uint32_t(*t1)[TWP] = c + TW;   // C_kk V, then X_kk
+    uint32_t(*ys)[TWP] = t1 + TW;  // 32 rows: X_k,j of the CTA's columns
+    uint32_t(*us)[TWP] = ys + 32;  // 32 rows: U_k,j
     const FieldP f = s.f;
     const int nb = s.nb;
     const int64_t k0 = s.k0, k1 = k0 + nb, rest = s.n - k1;
-    const int l = threadIdx.x % TB, r = threadIdx.x / TB;
-    if (blockIdx.x == 0 && s.xprev && r < s.nbprev && l < s.nbprev && r <= l)
-        s.C[(s.kprev + r) * s.ldc + s.kprev + l] = s.xprev[r * TB + l];
-    const bool in = r < nb && l < nb && r <= l;
-    const bool sq = r < nb && l < nb;
-    u[r][l] = in ? rd(s.U, s.ldu, k0 + r, k0 + l, f) : 0u;
-    vv[r][l] = s.V[(k0 / TB) * TB * TB + r * TB + l];  // zero outside the upper nb x nb triangle
-    c[r][l] = sq ? rd(s.C, s.ldc, k0 + (r < l ? r : l), k0 + (r < l ? l : r), f) : 0u;  // C_kk is symmetric
+    const int tid = threadIdx.x;
+    const int r = tid >> 4, l0 = tid & 15;  // outputs (r, l0 + 16 q)
+    if (blockIdx.x == 0 && s.xprev)
+        for (int q = 0; q < 4; ++q) {
+            const int l = l0 + 16 * q;
+            if (r < s.nbprev && l < s.nbprev && r <= l)
+                s.C[(s.kprev + r) * s.ldc + s.kprev + l] = s.xprev[r * TW + l];
+        }
+    for (int q = 0; q < 4; ++q) {
+        const int l = l0 + 16 * q;
+        const bool sq = r < nb && l < nb;
+        u[r][l] = (sq && r <= l) ? rd(s.U, s.ldu, k0 + r, k0 + l, f) : 0u;
+        vv[r][l] = s.V[(k0 / TW) * TW * TW + r * TW + l];  // zero outside the upper nb x nb triangle
+        c[r][l] = sq ? rd(s.C, s.ldc, k0 + (r < l ? r : l), k0 + (r < l ? l : r), f) : 0u;  // symmetric
+    }
     __syncthreads();
     // ---- X_kk: T1 = C V, S = V^T T1, M from S, X = M U ----
     {
-        uint64_t acc = 0;
-        for (int k = 0; k <= l; ++k) mac2<BIG>(acc, c[r][k], vv[k][l], f);
-        t1[r][l] = fp_reduce64_fold(acc, f);
+        uint64_t acc[4] = {0, 0, 0, 0};
+        for (int k = 0; k < TW; ++k) {
+            const uint32_t crk = c[r][k];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) mac2<BIG>(acc[q], crk, vv[k][l0 + 16 * q], f);  // V upper: 0 for k > l
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) t1[r][l0 + 16 * q] = fp_reduce64_fold(acc[q], f);
     }
     __syncthreads();
-    uint32_t mrl = 0;
-    if (r <= l) {
-        uint64_t acc = 0;
-        for (int k = 0; k <= r; ++k) mac2<BIG>(acc, vv[k][r], t1[k][l], f);
-        const uint32_t srl = fp_reduce64_fold(acc, f);
-        if (r < l) mrl = srl;
-        else if (f.p != 2u) mrl = fp_mul(srl, f.inv2, f);
-        else if (srl != 0u && r < nb && blockIdx.x == 0) atomicCAS(s.status, 0, LDLT_ERR_INCONSISTENT);
+    uint32_t mrl[4];
+    {
+        uint64_t acc[4] = {0, 0, 0, 0};
+        for (int k = 0; k <= r; ++k) {
+            const uint32_t vkr = vv[k][r];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) mac2<BIG>(acc[q], vkr, t1[k][l0 + 16 * q], f);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int l = l0 + 16 * q;
+            const uint32_t srl = fp_reduce64_fold(acc[q], f);
+            mrl[q] = 0u;
+            if (r < l) mrl[q] = srl;
+            else if (r == l) {
+                if (f.p != 2u) mrl[q] = fp_mul(srl, f.inv2, f);
+                else if (srl != 0u && r < nb && blockIdx.x == 0) atomicCAS(s.status, 0, LDLT_ERR_INCONSISTENT);
+            }
+        }
     }
     __syncthreads();
-    c[r][l] = mrl;  // M (C_kk is no longer needed)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) c[r][l0 + 16 * q] = mrl[q];  // M (C_kk is no longer needed)
     __syncthreads();
     {
-        uint64_t acc = 0;
-        for (int k = r; k <= l; ++k) mac2<BIG>(acc, c[r][k], u[k][l], f);
-        x[r][l] = r <= l ? fp_reduce64_fold(acc, f) : 0u;
+        uint64_t acc[4] = {0, 0, 0, 0};
+        for (int k = r; k < TW; ++k) {
+            const uint32_t mrk = c[r][k];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) mac2<BIG>(acc[q], mrk, u[k][l0 + 16 * q], f);  // U upper: 0 for k > l
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) t1[r][l0 + 16 * q] = fp_reduce64_fold(acc[q], f);  // X_kk
     }
     __syncthreads();
-    if (blockIdx.x == 0 && in) {
-        if (rest > 0) s.xcur[r * TB + l] = x[r][l];
-        else s.C[(k0 + r) * s.ldc + k0 + l] = x[r][l];
-    }
-    // ---- panel column j (warp r, lane l = block row) ----
-    const int warp = r, lane = l;
-    const int64_t i = (int64_t)blockIdx.x * TB + warp;  // trailing index
+    uint32_t(*x)[TWP] = t1;
+    if (blockIdx.x == 0)
+        for (int q = 0; q < 4; ++q) {
+            const int l = l0 + 16 * q;
+            if (r < nb && l < nb && r <= l) {
+                if (rest > 0) s.xcur[r * TW + l] = x[r][l];
+                else s.C[(k0 + r) * s.ldc + k0 + l] = x[r][l];
+            }
+        }
+    // ---- panel column j (warp w, lane: block rows lane and lane + 32) ----
+    const int warp = tid >> 5, lane = tid & 31;
+    const int64_t i = (int64_t)blockIdx.x * 32 + warp;  // trailing index
     const int64_t j = k1 + i;
-    uint32_t y = 0, ucj = 0;
+    uint32_t y[2] = {0u, 0u}, ucj[2] = {0u, 0u};
     if (i < rest) {
-        const bool row = lane < nb;
-        ucj = row ? rd(s.U, s.ldu, k0 + lane, j, f) : 0u;
-        const uint32_t ccj = row ? rd(s.C, s.ldc, k0 + lane, j, f) : 0u;
-        uint64_t acc = 0;
-        for (int k = 0; k < nb; ++k) {  // sum_{k <= lane} x_k,lane u_kj (x is upper triangular)
-            const uint32_t ukj = __shfl_sync(0xffffffffu, ucj, k);
-            mac2<BIG>(acc, x[k][lane], ukj, f);
+        uint32_t ccj[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int b = lane + 32 * h;
+            ucj[h] = b < nb ? rd(s.U, s.ldu, k0 + b, j, f) : 0u;
+            ccj[h] = b < nb ? rd(s.C, s.ldc, k0 + b, j, f) : 0u;
         }
-        const uint32_t t = fp_sub(ccj, fp_reduce64_fold(acc, f), f);
-        acc = 0;
+        uint64_t a0 = 0, a1 = 0;
+        for (int k = 0; k < nb; ++k) {  // sum_{k <= b} x_kb u_kj (x is upper triangular)
+            const uint32_t ukj = __shfl_sync(0xffffffffu, k < 32 ? ucj[0] : ucj[1], k & 31);
+            mac2<BIG>(a0, x[k][lane], ukj, f);
+            mac2<BIG>(a1, x[k][lane + 32], ukj, f);
+        }
+        const uint32_t t0 = fp_sub(ccj[0], fp_reduce64_fold(a0, f), f);
+        const uint32_t t1v = fp_sub(ccj[1], fp_reduce64_fold(a1, f), f);
+        a0 = 0; a1 = 0;
         for (int k = 0; k < nb; ++k) {  // y = V^T t
-            const uint32_t tk = __shfl_sync(0xffffffffu, t, k);
-            mac2<BIG>(acc, vv[k][lane], tk, f);
+            const uint32_t tk = __shfl_sync(0xffffffffu, k < 32 ? t0 : t1v, k & 31);
+            mac2<BIG>(a0, vv[k][lane], tk, f);
+            mac2<BIG>(a1, vv[k][lane + 32], tk, f);
         }
-        y = row ? fp_reduce64_fold(acc, f) : 0u;
-        if (row) s.C[(k0 + lane) * s.ldc + j] = y;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int b = lane + 32 * h;
+            y[h] = b < nb ? fp_reduce64_fold(h ? a1 : a0, f) : 0u;
+            if (b < nb) s.C[(k0 + b) * s.ldc + j] = y[h];
+        }
     }
     if (SPLIT) {
         const int np = 2 * nb, kpad = (np + 63) / 64 * 64;
         const int rows = (int)((rest + TC_BM - 1) / TC_BM * TC_BM), kprime = s.sa.la * kpad;
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (blockIdx.x == 0 && tid == 0) {
             s.out->m_next = (int)rest;
             s.out->np = np;
             s.out->abort = 0;
         }
-        ys[warp][lane] = y;
-        us[warp][lane] = ucj;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            ys[warp][lane + 32 * h] = y[h];
+            us[warp][lane + 32 * h] = ucj[h];
+        }
         __syncthreads();
-        // thread t < TB * kpad / 8 forms columns 8g .. 8g+7 (g = t mod kpad/8) of
+        // thread t < 32 * kpad / 8 forms columns 8g .. 8g+7 (g = t mod kpad/8) of
         // the CTA's row t / (kpad/8): G = [X | U], GD = [U | X]
         const int ng = kpad / 8;
-        const int t = threadIdx.x, w = t / ng, g = t % ng;
-        const int64_t iw = (int64_t)blockIdx.x * TB + w;
-        if (w < TB && iw < rows) {
+        const int w = tid / ng, g = tid % ng;
+        const int64_t iw = (int64_t)blockIdx.x * 32 + w;
+        if (w < 32 && iw < rows) {
             int32_t gd_bal[8];
             uint32_t gk[8];
 #pragma unroll
@@ -425,8 +501,8 @@ void trss_layout(int64_t n, uint32_t p, TrssLayout &L)
     L.out = take(sizeof(PanelOut));
     L.sigma = take((size_t)(n > 0 ? n : 1) * 4);
     const int64_t nn = n > 0 ? n : 1;
-    L.uinv = take((size_t)round_up(nn, TB) * TB * 4);  // U_kk^{-1} of every diagonal block
-    L.xblk = take((size_t)2 * TB * TB * 4);
+    L.uinv = take((size_t)round_up(nn, TW) * TW * 4);  // U_kk^{-1} of every diagonal block
+    L.xblk = take((size_t)2 * TW * TW * 4);
     L.opA = take(tc_operand_bytes(nn, limbs));
     L.opB = L.opA + (size_t)round_up(round_up(nn, 128) * (int64_t)limbs * KP_MAX * 2, 256);
     L.total = off;
@@ -480,42 +556,55 @@ extern "C" int ldlt_rpm_trss_ws(int64_t n, uint32_t p, const uint32_t *U, int64_
     uint32_t *V = (uint32_t *)(w + Lo.uinv);
     uint32_t *xblk = (uint32_t *)(w + Lo.xblk);
     const bool big = p >= (1u << 28);
-    const unsigned nblk = (unsigned)((n + TB - 1) / TB);
+    const unsigned nblk = (unsigned)((n + TW - 1) / TW);
     if (big) trss_vinv_kernel<true><<<nblk, 32, 0, st>>>(U, ldu, n, V, status, f);
     else trss_vinv_kernel<false><<<nblk, 32, 0, st>>>(U, ldu, n, V, status, f);
+    if (cudaFuncSetAttribute(trss_step_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)STEP_SMEM) != cudaSuccess ||
+        cudaFuncSetAttribute(trss_step_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)STEP_SMEM) != cudaSuccess ||
+        cudaFuncSetAttribute(trss_step_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)STEP_SMEM) != cudaSuccess ||
+        cudaFuncSetAttribute(trss_step_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)STEP_SMEM) != cudaSuccess)
+        return LDLT_ERR_CUDA;
     TrssStep sp;
     sp.n = n; sp.ldu = ldu; sp.ldc = ldc; sp.U = U; sp.V = V; sp.C = C; sp.status = status; sp.f = f;
     sp.sa = tc_split_args(f, limbs, opA, opB);
     sp.out = out;
     sp.xprev = nullptr; sp.kprev = 0; sp.nbprev = 0;
-    for (int64_t k0 = 0, step = 0; k0 < n; k0 += TB, ++step) {
-        const int nb = (int)((n - k0) < TB ? (n - k0) : TB);
+    for (int64_t k0 = 0, step = 0; k0 < n; k0 += TW, ++step) {
+        const int nb = (int)((n - k0) < TW ? (n - k0) : TW);
         const int64_t k1 = k0 + nb, rest = n - k1;
         const bool tc = rest >= TRSS_TC_MIN;
         sp.k0 = k0; sp.nb = nb;
-        sp.xcur = xblk + (step & 1) * TB * TB;
-        // one CTA per TB trailing columns (tensor form: per TB operand rows, padded to 128)
+        sp.xcur = xblk + (step & 1) * TW * TW;
+        // one CTA per 32 trailing columns (tensor form: per 32 operand rows, padded to 128)
         const int64_t cols = tc ? round_up(rest, 128) : rest;
-        const unsigned grid = (unsigned)(cols > 0 ? (cols + TB - 1) / TB : 1);
+        const unsigned grid = (unsigned)(cols > 0 ? (cols + 31) / 32 : 1);
         if (tc) {
-            if (big) trss_step_kernel<true, true><<<grid, TB * TB, 0, st>>>(sp);
-            else trss_step_kernel<false, true><<<grid, TB * TB, 0, st>>>(sp);
+            if (big) trss_step_kernel<true, true><<<grid, STEP_THREADS, STEP_SMEM, st>>>(sp);
+            else trss_step_kernel<false, true><<<grid, STEP_THREADS, STEP_SMEM, st>>>(sp);
         } else {
-            if (big) trss_step_kernel<true, false><<<grid, TB * TB, 0, st>>>(sp);
-            else trss_step_kernel<false, false><<<grid, TB * TB, 0, st>>>(sp);
+            if (big) trss_step_kernel<true, false><<<grid, STEP_THREADS, STEP_SMEM, st>>>(sp);
+            else trss_step_kernel<false, false><<<grid, STEP_THREADS, STEP_SMEM, st>>>(sp);
         }
         sp.xprev = sp.xcur; sp.kprev = k0; sp.nbprev = nb;
         if (rest <= 0) continue;
         if (tc) {
-            // C_rr -= X^T U + U^T X on tensor cores: the SYRDK kernel on C's upper triangle
+            // C_rr -= X^T U + U^T X on tensor cores: the SYRDK kernel on C's upper triangle (K = 2 nb)
             uint32_t *blk = C + k1 * ldc + k1;
             if (launch_syrdk_tc(blk, ldc, sigma, ls, out, opA, opB, limbs, f, blk, 2000000000LL, status, nsm, 0,
                                 st, 1) != cudaSuccess)
                 return LDLT_ERR_CUDA;
         } else {
+            // CUDA cores, the block's rows in halves of TB (the tile kernel holds TB rows)
             const unsigned gp = (unsigned)((rest + TC - 1) / TC);
-            if (big) trss_syr2k_kernel<true><<<dim3(gp, gp), 256, 0, st>>>(k0, nb, n, U, ldu, C, ldc, f);
-            else trss_syr2k_kernel<false><<<dim3(gp, gp), 256, 0, st>>>(k0, nb, n, U, ldu, C, ldc, f);
+            for (int h = 0; h < nb; h += TB) {
+                const int nh = nb - h < TB ? nb - h : TB;
+                if (big) trss_syr2k_kernel<true><<<dim3(gp, gp), 256, 0, st>>>(k0 + h, nh, k1, n, U, ldu, C, ldc, f);
+                else trss_syr2k_kernel<false><<<dim3(gp, gp), 256, 0, st>>>(k0 + h, nh, k1, n, U, ldu, C, ldc, f);
+            }
         }
     }
     return cudaGetLastError() == cudaSuccess ? LDLT_OK : LDLT_ERR_CUDA;
@@ -546,9 +635,9 @@ extern "C" int ldlt_rpm_trss(int64_t n, uint32_t p, const uint32_t *U, int64_t l
         else
             trss_panel_kernel<false><<<gw, PW * 32, 0, st>>>(k0, nb, n, U, ldu, C, ldc, f);
         if (p >= (1u << 28))
-            trss_syr2k_kernel<true><<<dim3(gp, gp), 256, 0, st>>>(k0, nb, n, U, ldu, C, ldc, f);
+            trss_syr2k_kernel<true><<<dim3(gp, gp), 256, 0, st>>>(k0, nb, k0 + nb, n, U, ldu, C, ldc, f);
         else
-            trss_syr2k_kernel<false><<<dim3(gp, gp), 256, 0, st>>>(k0, nb, n, U, ldu, C, ldc, f);
+            trss_syr2k_kernel<false><<<dim3(gp, gp), 256, 0, st>>>(k0, nb, k0 + nb, n, U, ldu, C, ldc, f);
     }
     return cudaGetLastError() == cudaSuccess ? LDLT_OK : LDLT_ERR_CUDA;
 }
